@@ -1,0 +1,206 @@
+/*
+ * survgpu.h - C ABI of libsurvgpu.so: penalised Cox (Breslow ties) and
+ * Fine-Gray regression by cyclic coordinate descent (CCD) on one GB300 GPU.
+ *
+ * The library computes, for one coordinate j at a time, the gradient and
+ * Hessian of the log partial likelihood (Cox, Eq. cox_l, Section 2.1) or of
+ * the log pseudo-likelihood (Fine-Gray, Eq. fg_l, Section 2.2) through risk-set
+ * prefix sums over subjects arranged by decreasing time (Section 2.7, Eqs.
+ * cox_g, cox_h, fg_g, fg_h), takes a trust-region Newton step on the L1/L2
+ * penalised objective (Sections 2.3, 2.4) and updates eta = X beta.  All of
+ * that runs in CUDA kernels; the host only validates sizes, stages buffers and
+ * reads the result.
+ *
+ * Memory: every array pointer may point to host memory or to device memory of
+ * the current device; the library asks the CUDA runtime which one it is.
+ * Host arrays are copied to device workspace inside the call (and results
+ * copied back), so a host-buffer call includes those transfers.  The caller
+ * owns every buffer it passes; the library never frees caller memory and keeps
+ * no pointer to it after the call returns.
+ *
+ * Threading: calls on different workspaces may run concurrently on different
+ * streams.  A workspace must not be used by two calls at the same time.
+ *
+ * Errors: every entry point returns SURV_OK (0) on success, a positive warning
+ * or a negative error code.  surv_strerror() names a code and
+ * surv_last_error() returns a message with details for the calling thread.
+ * On error no output array is written, except that beta_inout may hold the
+ * last iterate for SURV_W_NOT_CONVERGED and SURV_E_DEVICE_TIMEOUT.
+ */
+#ifndef SURVGPU_H
+#define SURVGPU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ------------------------------------------------------ */
+#define SURV_OK 0
+#define SURV_W_NOT_CONVERGED 1    /* max_sweeps reached; beta holds the last iterate */
+#define SURV_E_INVALID (-1)       /* null pointer, negative size, bad enum, bad j   */
+#define SURV_E_UNSORTED (-2)      /* time is not non-increasing                     */
+#define SURV_E_STATUS (-3)        /* status code outside {0,1} (Cox) / {0,1,2} (FG)  */
+#define SURV_E_NONFINITE (-4)     /* NaN or Inf in X, beta or penalty factors        */
+#define SURV_E_NO_EVENTS (-5)     /* no event (Cox) / no primary event (FG)          */
+#define SURV_E_CUDA (-6)          /* a CUDA runtime call failed                      */
+#define SURV_E_DEVICE_TIMEOUT (-7)/* a device-side wait gave up (bounded spin)       */
+#define SURV_E_NOMEM (-8)         /* device allocation failed                        */
+#define SURV_E_INDEX (-9)         /* CSC col_ptr/row_idx malformed or out of range   */
+
+/* ---- enumerations ------------------------------------------------------ */
+#define SURV_CSC 0            /* column-compressed: col_ptr, row_idx, values   */
+#define SURV_DENSE 1          /* dense column-major, leading dimension n        */
+
+#define SURV_F32 0
+#define SURV_F64 1
+
+#define SURV_COX 0
+#define SURV_FG 1
+
+#define SURV_PEN_NONE 0
+#define SURV_PEN_L1 1         /* pi = -sum_j lambda pf_j |beta_j|       (Section 2.3) */
+#define SURV_PEN_L2 2         /* pi = -sum_j lambda pf_j beta_j^2 / 2  (1/tau = lambda pf) */
+
+#define SURV_PREC_F32C 0      /* FP32 exp/scans with float-float (compensated) carries,
+                                 FP64 Newton step, logs and final scalars            */
+#define SURV_PREC_F64 1       /* FP64 throughout                                     */
+
+/* ---- data -------------------------------------------------------------- */
+/* Survival data in decreasing-time order (Section 2.7).
+ *   time    [n]  int32, non-increasing (validated: SURV_E_UNSORTED).  Use
+ *                surv_sort_desc() to obtain the order of unsorted data.
+ *   status  [n]  int8: 0 censored, 1 event (Cox) / primary event (FG),
+ *                2 competing event (FG only).
+ *   layout = SURV_CSC:
+ *     col_ptr [p+1] int64, col_ptr[0] = 0, non-decreasing; nnz = col_ptr[p].
+ *     row_idx [nnz] int32, strictly increasing inside each column, in [0,n).
+ *     values  [nnz] of dtype, or NULL for an all-ones (indicator) matrix.
+ *   layout = SURV_DENSE:
+ *     values  [n*p] of dtype, column-major (element (i,j) at j*n+i);
+ *     col_ptr and row_idx are ignored.
+ */
+typedef struct surv_data {
+  int64_t n;
+  int64_t p;
+  const int32_t *time;
+  const int8_t *status;
+  int32_t layout;
+  int32_t dtype;
+  const int64_t *col_ptr;
+  const int32_t *row_idx;
+  const void *values;
+} surv_data;
+
+typedef struct surv_workspace surv_workspace;   /* opaque device workspace */
+
+/* ---- options ----------------------------------------------------------- */
+typedef struct surv_opts {
+  int32_t penalty;               /* SURV_PEN_*                                      */
+  int32_t precision;             /* SURV_PREC_*                                     */
+  double lambda;                 /* L1: gamma; L2: 1/tau (Section 2.3)              */
+  const double *penalty_factor;  /* [p] multiplier per coordinate (0 = unpenalised),
+                                    host or device, or NULL for all ones            */
+  double tol;                    /* stop when |f_k - f_{k-1}| / |f_k| < tol after a
+                                    sweep, f = loglik + penalty                     */
+  int32_t max_sweeps;            /* cap on full sweeps (>= 0)                       */
+  int32_t flags;                 /* SURV_FLAG_* bits, normally 0                    */
+  double wait_limit_s;           /* bound on every device-side wait of the grid-wide
+                                    exchange; <= 0 selects 2 seconds                */
+  void *stream;                  /* cudaStream_t, or NULL for the default stream    */
+  surv_workspace *workspace;     /* reusable workspace, or NULL (allocate per call) */
+} surv_opts;
+
+/* Test only: one CTA of the CCD kernel never announces its first exchange,
+ * so every other CTA's bounded wait expires; the call must then return
+ * SURV_E_DEVICE_TIMEOUT and leave the device usable. */
+#define SURV_FLAG_TEST_STALL 1
+
+/* Fill *opts with defaults: no penalty, FP32-compensated precision,
+ * tol 1e-8, max_sweeps 1000, default stream, no workspace. */
+void surv_opts_default(surv_opts *opts);
+
+typedef struct surv_fit_info {
+  int32_t sweeps;                /* full sweeps performed                         */
+  int32_t converged;             /* 1 if the tolerance test passed                */
+  int32_t nnz_beta;              /* nonzero coefficients at exit                  */
+  int32_t device_error;          /* device error word (0 = none)                  */
+  double loglik;                 /* log (pseudo-)likelihood at the returned beta  */
+  double objective;              /* loglik + penalty at the returned beta         */
+  double objective_prev;         /* the same after the previous sweep             */
+  int64_t n_groups;              /* number of tie groups K                        */
+  int64_t coordinate_passes;     /* risk-set passes run (sweeps * p + 1)          */
+  int64_t eta_updates;           /* coordinates whose step was nonzero            */
+  int64_t kernel_launches;       /* CUDA kernels launched by this call            */
+  double ccd_kernel_ms;          /* device time of the CCD kernel (CUDA events on
+                                    the call's stream)                            */
+} surv_fit_info;
+
+/* ---- entry points ------------------------------------------------------ */
+
+/* Workspace that caches device buffers between calls on the same device.
+ * surv_workspace_create: *ws receives a new handle (SURV_E_INVALID if ws is
+ * NULL).  surv_workspace_destroy frees its device memory (NULL is a no-op). */
+int surv_workspace_create(surv_workspace **ws);
+int surv_workspace_destroy(surv_workspace *ws);
+
+/* Stable order of decreasing time (Section 2.7 arranges subjects by
+ * decreasing observed time; ties keep input order, so the result is unique).
+ *   time [n] int32 (host or device), perm [n] int32 output (host or device):
+ *   perm[r] = input index of the subject at rank r.
+ * Device LSD radix sort; the stream is used for all work.  n = 0 is a no-op. */
+int surv_sort_desc(const int32_t *time, int64_t n, int32_t *perm, void *stream);
+
+/* Penalised Cox fit by CCD (Sections 2.1, 2.3, 2.4, 2.7).
+ *   beta_inout [p] double (host or device): warm start on entry, estimate on
+ *   return.  info (host, may be NULL) receives the fit summary.
+ * Returns SURV_OK, SURV_W_NOT_CONVERGED or an error code. */
+int cox_fit(const surv_data *data, const surv_opts *opts, double *beta_inout,
+            surv_fit_info *info);
+
+/* Penalised Fine-Gray fit by CCD (Sections 2.2-2.4, 2.7); status 2 marks the
+ * competing event and the censoring weights use the Kaplan-Meier estimate of
+ * the censoring distribution computed on the device.  Same contract as
+ * cox_fit. */
+int fg_fit(const surv_data *data, const surv_opts *opts, double *beta_inout,
+           surv_fit_info *info);
+
+/* One risk-set pass (Section 2.7, steps 1-4) at beta for coordinate j:
+ *   *loglik = l(beta) (Eq. cox_l or fg_l), *grad = dl/dbeta_j,
+ *   *hess = d2l/dbeta_j^2 (Eqs. cox_g/cox_h or fg_g/fg_h), unpenalised.
+ *   model = SURV_COX or SURV_FG; beta [p] double host or device;
+ *   loglik/grad/hess: host doubles (any may be NULL).  opts may be NULL
+ *   (precision F32C, default stream, no workspace).  j in [0, p). */
+int loglik_grad_hess(const surv_data *data, int32_t model, const double *beta,
+                     int32_t j, double *loglik, double *grad, double *hess,
+                     const surv_opts *opts);
+
+/* Breslow tie-group table of data already in decreasing-time order
+ * (Section 2.7; the Fine-Gray weights of Section 2.2).
+ *   time [n] int32 non-increasing, status [n] int8 (host or device).
+ *   *K receives the number of groups (maximal runs of equal time).  If the
+ *   output arrays are non-NULL they must hold max_groups entries (host or
+ *   device) and receive: gend[k] = position of the last subject of group k,
+ *   dk[k] = subjects with status 1 in group k, Gk[k] = Kaplan-Meier estimate
+ *   of the censoring survival G(t_k) = prod_{t_k' <= t_k} (1 - c_k'/n_k')
+ *   with c = censored count and n = #{y >= t_k'}.
+ *   Returns SURV_E_INVALID if K > max_groups and an output is requested;
+ *   SURV_E_UNSORTED / SURV_E_STATUS on invalid input (status codes 0..2). */
+int surv_groups(const int32_t *time, const int8_t *status, int64_t n, int64_t max_groups, int64_t *K,
+                int32_t *gend, int32_t *dk, double *Gk, void *stream);
+
+/* Short name of a return code (static string). */
+const char *surv_strerror(int code);
+
+/* Details of the last error on the calling thread (static per thread). */
+const char *surv_last_error(void);
+
+/* Library version as 10000*major + 100*minor + patch. */
+int surv_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SURVGPU_H */

@@ -275,7 +275,8 @@ def fg_weights(time_sorted, status_sorted):
     # group index of every position: number of group ends strictly before it
     n = len(status_sorted)
     gid = np.searchsorted(gend, np.arange(n), side="left")
-    W = np.where(status_sorted == 2, 1.0 / Gk[gid], 0.0)
+    with np.errstate(divide="ignore"):   # G = 0 only in a group with no competing event
+        W = np.where(status_sorted == 2, 1.0 / Gk[gid], 0.0)
     return W, Gk, gend
 
 

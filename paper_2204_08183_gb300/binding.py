@@ -1,0 +1,296 @@
+"""Thin ctypes binding of libsurvgpu.so (include/survgpu.h).
+
+Argument marshalling only: arrays (torch tensors on the GPU or the CPU, or
+numpy arrays) are passed to the C ABI as raw pointers; every step of the
+computation runs in the library's CUDA kernels.  There is no CPU fallback:
+if the library is missing or no CUDA device is present, the calls raise.
+
+Names follow the C ABI: ``cox_fit``, ``fg_fit``, ``loglik_grad_hess``,
+``surv_sort_desc``, plus ``SurvData`` to describe a cohort and
+``Workspace`` for a reusable device workspace.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsurvgpu.so")
+
+SURV_OK = 0
+SURV_W_NOT_CONVERGED = 1
+SURV_E_INVALID = -1
+SURV_E_UNSORTED = -2
+SURV_E_STATUS = -3
+SURV_E_NONFINITE = -4
+SURV_E_NO_EVENTS = -5
+SURV_E_CUDA = -6
+SURV_E_DEVICE_TIMEOUT = -7
+SURV_E_NOMEM = -8
+SURV_E_INDEX = -9
+
+SURV_CSC, SURV_DENSE = 0, 1
+SURV_F32, SURV_F64 = 0, 1
+SURV_COX, SURV_FG = 0, 1
+SURV_PEN = {"none": 0, "l1": 1, "l2": 2}
+SURV_PREC = {"f32c": 0, "f64": 1}
+SURV_FLAG_TEST_STALL = 1
+
+# exported symbols, in the order the header declares them
+EXPORTS = ["surv_opts_default", "surv_workspace_create", "surv_workspace_destroy", "surv_sort_desc",
+           "cox_fit", "fg_fit", "loglik_grad_hess", "surv_groups", "surv_strerror", "surv_last_error",
+           "surv_version"]
+
+
+class surv_data(C.Structure):
+    _fields_ = [("n", C.c_int64), ("p", C.c_int64), ("time", C.c_void_p), ("status", C.c_void_p),
+                ("layout", C.c_int32), ("dtype", C.c_int32), ("col_ptr", C.c_void_p), ("row_idx", C.c_void_p),
+                ("values", C.c_void_p)]
+
+
+class surv_opts(C.Structure):
+    _fields_ = [("penalty", C.c_int32), ("precision", C.c_int32), ("lambda_", C.c_double),
+                ("penalty_factor", C.c_void_p), ("tol", C.c_double), ("max_sweeps", C.c_int32),
+                ("flags", C.c_int32), ("wait_limit_s", C.c_double), ("stream", C.c_void_p),
+                ("workspace", C.c_void_p)]
+
+
+class surv_fit_info(C.Structure):
+    _fields_ = [("sweeps", C.c_int32), ("converged", C.c_int32), ("nnz_beta", C.c_int32),
+                ("device_error", C.c_int32), ("loglik", C.c_double), ("objective", C.c_double),
+                ("objective_prev", C.c_double), ("n_groups", C.c_int64), ("coordinate_passes", C.c_int64),
+                ("eta_updates", C.c_int64), ("kernel_launches", C.c_int64), ("ccd_kernel_ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libsurvgpu.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libsurvgpu.so not found at %s: run paper_2204_08183_gb300.build.build()" % path)
+    lib = C.CDLL(path)
+    lib.surv_opts_default.argtypes = [C.POINTER(surv_opts)]
+    lib.surv_opts_default.restype = None
+    lib.surv_workspace_create.argtypes = [C.POINTER(C.c_void_p)]
+    lib.surv_workspace_destroy.argtypes = [C.c_void_p]
+    lib.surv_sort_desc.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]
+    for f in (lib.cox_fit, lib.fg_fit):
+        f.argtypes = [C.POINTER(surv_data), C.POINTER(surv_opts), C.c_void_p, C.POINTER(surv_fit_info)]
+        f.restype = C.c_int
+    lib.loglik_grad_hess.argtypes = [C.POINTER(surv_data), C.c_int32, C.c_void_p, C.c_int32,
+                                     C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                     C.POINTER(surv_opts)]
+    lib.surv_groups.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.POINTER(C.c_int64), C.c_void_p,
+                                C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.surv_strerror.argtypes = [C.c_int]
+    lib.surv_strerror.restype = C.c_char_p
+    lib.surv_last_error.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+class SurvError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (load().surv_strerror(code).decode(), code, msg))
+        self.code = code
+
+
+def _check(rc, allow=(SURV_OK,)):
+    if rc not in allow:
+        raise SurvError(rc, load().surv_last_error().decode())
+    return rc
+
+
+def _ptr(a):
+    """Raw address of a torch tensor or numpy array (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        if not (a.flags["C_CONTIGUOUS"] or a.flags["F_CONTIGUOUS"]):
+            raise ValueError("array must be contiguous")
+        return a.ctypes.data
+    raise TypeError("expected a torch tensor or a numpy array, got %r" % type(a))
+
+
+def _dtype_code(a):
+    name = str(a.dtype)
+    if name.endswith("float32"):
+        return SURV_F32
+    if name.endswith("float64"):
+        return SURV_F64
+    raise TypeError("values must be float32 or float64, got %s" % name)
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return stream
+
+
+class SurvData:
+    """A cohort in the library's layout (subjects in decreasing time order).
+
+    Dense X: a column-major (n, p) array -- a Fortran-ordered numpy array, or
+    a torch tensor holding X^T contiguously (shape (p, n)), passed with
+    ``layout="dense"``.  CSC: ``col_ptr`` (int64, p+1), ``row_idx`` (int32),
+    ``values`` (float32/float64 or None for indicators).  Arrays may live on
+    the host or on the GPU; references are kept alive by this object.
+    """
+
+    def __init__(self, time, status, *, X=None, col_ptr=None, row_idx=None, values=None, n=None, p=None):
+        self._keep = [time, status, X, col_ptr, row_idx, values]
+        self.time, self.status = time, status
+        n = int(time.shape[0]) if n is None else int(n)
+        s = surv_data()
+        s.n = n
+        s.time = _ptr(time)
+        s.status = _ptr(status)
+        if X is not None:
+            if isinstance(X, np.ndarray):
+                if X.ndim != 2 or X.shape[0] != n or not X.flags["F_CONTIGUOUS"]:
+                    raise ValueError("dense X must be a Fortran-ordered (n, p) array")
+                p = X.shape[1]
+            else:  # torch: expect the (p, n) row-major transpose
+                if X.dim() != 2 or X.shape[1] != n:
+                    raise ValueError("dense torch X must have shape (p, n) (column-major X)")
+                p = X.shape[0]
+            s.layout = SURV_DENSE
+            s.dtype = _dtype_code(X)
+            s.values = _ptr(X)
+        else:
+            p = int(col_ptr.shape[0]) - 1 if p is None else int(p)
+            s.layout = SURV_CSC
+            s.dtype = _dtype_code(values) if values is not None else SURV_F32
+            s.col_ptr = _ptr(col_ptr)
+            s.row_idx = _ptr(row_idx)
+            s.values = _ptr(values)
+        s.p = int(p)
+        self.n, self.p = n, int(p)
+        self.c = s
+
+
+class Workspace:
+    """Reusable device workspace (surv_workspace)."""
+
+    def __init__(self):
+        h = C.c_void_p()
+        _check(load().surv_workspace_create(C.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            load().surv_workspace_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_opts(penalty="none", lam=0.0, penalty_factor=None, tol=1e-8, max_sweeps=1000, precision="f32c",
+              stream=None, workspace=None, flags=0, wait_limit_s=0.0):
+    o = surv_opts()
+    load().surv_opts_default(C.byref(o))
+    o.penalty = SURV_PEN[penalty]
+    o.precision = SURV_PREC[precision]
+    o.lambda_ = float(lam)
+    o.penalty_factor = _ptr(penalty_factor)
+    o.tol = float(tol)
+    o.max_sweeps = int(max_sweeps)
+    o.flags = int(flags)
+    o.wait_limit_s = float(wait_limit_s)
+    o.stream = _stream(stream)
+    o.workspace = workspace.handle if workspace is not None else None
+    return o
+
+
+def _fit(fn, data, beta, allow_not_converged, **kw):
+    opts = make_opts(**kw)
+    if beta is None:
+        beta = np.zeros(data.p, dtype=np.float64)
+    info = surv_fit_info()
+    rc = fn(C.byref(data.c), C.byref(opts), C.c_void_p(_ptr(beta)), C.byref(info))
+    allow = (SURV_OK, SURV_W_NOT_CONVERGED) if allow_not_converged else (SURV_OK,)
+    _check(rc, allow)
+    return beta, info.as_dict(), rc
+
+
+def cox_fit(data: SurvData, beta=None, allow_not_converged=True, **kw):
+    """Penalised Cox CCD fit.  ``beta`` (float64, host or device) is the warm
+    start and receives the estimate.  Returns (beta, info dict, return code)."""
+    return _fit(load().cox_fit, data, beta, allow_not_converged, **kw)
+
+
+def fg_fit(data: SurvData, beta=None, allow_not_converged=True, **kw):
+    """Penalised Fine-Gray CCD fit; same contract as cox_fit."""
+    return _fit(load().fg_fit, data, beta, allow_not_converged, **kw)
+
+
+def loglik_grad_hess(data: SurvData, model: str, beta, j: int, **kw):
+    """(l, dl/dbeta_j, d2l/dbeta_j^2) at beta, computed on the GPU."""
+    opts = make_opts(**kw)
+    l, g, h = C.c_double(), C.c_double(), C.c_double()
+    m = {"cox": SURV_COX, "fg": SURV_FG}[model]
+    rc = load().loglik_grad_hess(C.byref(data.c), m, C.c_void_p(_ptr(beta)), int(j), C.byref(l), C.byref(g),
+                                 C.byref(h), C.byref(opts))
+    _check(rc)
+    return l.value, g.value, h.value
+
+
+def surv_sort_desc(time, perm=None, stream=None):
+    """Stable decreasing-time order of ``time`` (int32); returns ``perm``."""
+    n = int(time.shape[0])
+    if perm is None:
+        if hasattr(time, "data_ptr"):
+            import torch
+            perm = torch.empty(n, dtype=torch.int32, device=time.device)
+        else:
+            perm = np.empty(n, dtype=np.int32)
+    rc = load().surv_sort_desc(C.c_void_p(_ptr(time)), n, C.c_void_p(_ptr(perm)), _stream(stream))
+    _check(rc)
+    return perm
+
+
+def surv_groups(time, status, stream=None):
+    """Tie-group table of sorted data: (gend int32[K], dk int32[K], Gk float64[K]) as numpy arrays."""
+    n = int(time.shape[0])
+    K = C.c_int64()
+    lib = load()
+    st = _stream(stream)
+    _check(lib.surv_groups(C.c_void_p(_ptr(time)), C.c_void_p(_ptr(status)), n, 0, C.byref(K), None, None, None, st))
+    k = K.value
+    gend = np.empty(k, np.int32)
+    dk = np.empty(k, np.int32)
+    Gk = np.empty(k, np.float64)
+    if k:
+        _check(lib.surv_groups(C.c_void_p(_ptr(time)), C.c_void_p(_ptr(status)), n, k, C.byref(K),
+                               C.c_void_p(gend.ctypes.data), C.c_void_p(dk.ctypes.data),
+                               C.c_void_p(Gk.ctypes.data), st))
+    return gend, dk, Gk
+
+
+def strerror(code: int) -> str:
+    return load().surv_strerror(code).decode()

@@ -1,0 +1,580 @@
+// C ABI of libsurvgpu.so (declared in include/survgpu.h): argument checks,
+// staging of host buffers, workspace management and the launch sequence
+// prep kernels -> persistent CCD kernel.  No arithmetic of the method runs
+// on the host; the host reads back only sizes, error words and results.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "survgpu.h"
+
+struct surv_workspace {
+  struct Buf {
+    void* p = nullptr;
+    size_t cap = 0;
+  };
+  enum Id {
+    TIME, STATUS, COLPTR, ROWIDX, VALUES, XD, E, ETA, W2, GEND, DK, CK, GK, WK0, WOFF, DTX, BETA, WIDTH, PEN, REC,
+    SLOTS, CTRL, BLOCKCNT, SORTWORK, PERM, PF, NBUF
+  };
+  int device = -1;
+  Buf bufs[NBUF];
+};
+
+namespace {
+
+using survgpu::CcdParams;
+
+thread_local char g_last_error[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+  va_end(ap);
+}
+
+struct DevCtrl {
+  unsigned perr;
+  unsigned err;
+  int32_t K;
+  int32_t total_events;
+  unsigned counters[2];
+  unsigned pad[2];
+  double out[survgpu::OUT_COUNT];
+};
+
+// Allocation failures map to SURV_E_NOMEM, anything else to SURV_E_CUDA.
+int cuda_code(cudaError_t e) { return e == cudaErrorMemoryAllocation ? SURV_E_NOMEM : SURV_E_CUDA; }
+
+#define CUDA_TRY(call)                                                          \
+  do {                                                                          \
+    cudaError_t e_ = (call);                                                    \
+    if (e_ != cudaSuccess) {                                                    \
+      set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+      return cuda_code(e_);                                                     \
+    }                                                                           \
+  } while (0)
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+int ensure(surv_workspace* ws, int id, size_t bytes, void** out) {
+  auto& b = ws->bufs[id];
+  if (bytes == 0) bytes = 256;
+  if (b.cap < bytes) {
+    if (b.p) {
+      cudaError_t e = cudaFree(b.p);
+      b.p = nullptr;
+      b.cap = 0;
+      if (e != cudaSuccess) {
+        set_error("cudaFree: %s", cudaGetErrorString(e));
+        return SURV_E_CUDA;
+      }
+    }
+    cudaError_t e = cudaMalloc(&b.p, align256(bytes));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      b.p = nullptr;
+      set_error("cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+      return SURV_E_NOMEM;
+    }
+    b.cap = align256(bytes);
+  }
+  *out = b.p;
+  return SURV_OK;
+}
+
+void free_all(surv_workspace* ws) {
+  for (auto& b : ws->bufs) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+  }
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Device view of a caller array: the pointer itself if it is device memory,
+// else a workspace copy made on `s`.
+int device_view(surv_workspace* ws, int id, const void* src, size_t bytes, cudaStream_t s, const void** out) {
+  if (is_device_ptr(src) || bytes == 0) {
+    *out = src;
+    return SURV_OK;
+  }
+  void* d = nullptr;
+  int rc = ensure(ws, id, bytes, &d);
+  if (rc) return rc;
+  CUDA_TRY(cudaMemcpyAsync(d, src, bytes, cudaMemcpyHostToDevice, s));
+  *out = d;
+  return SURV_OK;
+}
+
+// Copy a caller array (host or device) into host memory.
+int to_host(const void* src, size_t bytes, void* dst, cudaStream_t s) {
+  if (bytes == 0) return SURV_OK;
+  CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return SURV_OK;
+}
+
+struct WsGuard {
+  surv_workspace* ws = nullptr;
+  bool owned = false;
+  ~WsGuard() {
+    if (owned && ws) {
+      free_all(ws);
+      delete ws;
+    }
+  }
+};
+
+int map_prep_error(unsigned perr) {
+  if (perr & survgpu::PREP_INDEX) { set_error("CSC row indices out of range or not increasing"); return SURV_E_INDEX; }
+  if (perr & survgpu::PREP_UNSORTED) { set_error("time is not non-increasing"); return SURV_E_UNSORTED; }
+  if (perr & survgpu::PREP_STATUS) { set_error("status code out of range"); return SURV_E_STATUS; }
+  if (perr & survgpu::PREP_NONFINITE) { set_error("non-finite value in X, beta or penalty factors"); return SURV_E_NONFINITE; }
+  return SURV_OK;
+}
+
+int fit_common(int model, const surv_data* d, const surv_opts* o_in, double* beta_inout, surv_fit_info* info,
+               int single_j, double* out_l, double* out_g, double* out_h) {
+  g_last_error[0] = '\0';
+  surv_opts o;
+  if (o_in) o = *o_in; else surv_opts_default(&o);
+  if (!d || !beta_inout) { set_error("null data or beta"); return SURV_E_INVALID; }
+  const int64_t n = d->n, p = d->p;
+  if (n < 0 || p < 1 || n > 0x7fffffff || p > 0x7fffffff) { set_error("bad sizes n=%lld p=%lld", (long long)n, (long long)p); return SURV_E_INVALID; }
+  if (d->layout != SURV_CSC && d->layout != SURV_DENSE) { set_error("bad layout"); return SURV_E_INVALID; }
+  if (d->dtype != SURV_F32 && d->dtype != SURV_F64) { set_error("bad dtype"); return SURV_E_INVALID; }
+  if (o.penalty < 0 || o.penalty > 2 || o.precision < 0 || o.precision > 1) { set_error("bad penalty/precision"); return SURV_E_INVALID; }
+  if (!(o.lambda >= 0.0) || !std::isfinite(o.lambda) || !(o.tol >= 0.0) || o.max_sweeps < 0) { set_error("bad lambda/tol/max_sweeps"); return SURV_E_INVALID; }
+  if ((o.flags & ~SURV_FLAG_TEST_STALL) != 0) { set_error("unknown flags"); return SURV_E_INVALID; }
+  if (single_j >= 0 && single_j >= p) { set_error("coordinate j=%d out of range", single_j); return SURV_E_INVALID; }
+  if (n == 0) { set_error("no subjects"); return SURV_E_NO_EVENTS; }
+  if (!d->time || !d->status) { set_error("null time/status"); return SURV_E_INVALID; }
+  if (d->layout == SURV_CSC && (!d->col_ptr || !d->row_idx)) { set_error("null CSC arrays"); return SURV_E_INVALID; }
+  if (d->layout == SURV_DENSE && !d->values) { set_error("null dense values"); return SURV_E_INVALID; }
+
+  cudaStream_t s = static_cast<cudaStream_t>(o.stream);
+  int64_t launches = 0;
+  WsGuard guard;
+  surv_workspace* ws = o.workspace;
+  if (!ws) {
+    ws = new surv_workspace();
+    guard.ws = ws;
+    guard.owned = true;
+  }
+  CUDA_TRY(cudaGetDevice(&ws->device));
+  const int prec = o.precision;              // 0: float / float-float, 1: double
+  const size_t tsz = prec == 0 ? 4 : 8;
+  const int layout = d->layout;
+  const int M = model == SURV_COX ? 3 : 6;
+  using W = surv_workspace;
+
+  int G = 0, wpc = 0;
+  CUDA_TRY(survgpu::ccd_grid_size(model, layout, prec, &G, &wpc));
+  if (G < 1) { set_error("CCD kernel cannot be made co-resident"); return SURV_E_CUDA; }
+  const int32_t nwarps = G * wpc;
+  const int64_t nwords = (n + 31) / 32;
+  const int32_t wpw = (int32_t)((nwords + nwarps - 1) / nwarps);
+  const int64_t rows_per_warp = (int64_t)wpw * 32;
+
+  // ---------------------------------------------------------- staging
+  int rc;
+  const void *time_d = nullptr, *status_d = nullptr, *colptr_d = nullptr, *rowidx_d = nullptr, *vals_d = nullptr;
+  if ((rc = device_view(ws, W::TIME, d->time, 4 * (size_t)n, s, &time_d))) return rc;
+  if ((rc = device_view(ws, W::STATUS, d->status, (size_t)n, s, &status_d))) return rc;
+  int64_t nnz = 0;
+  std::vector<int64_t> colptr_h;
+  if (layout == SURV_CSC) {
+    colptr_h.resize(p + 1);
+    if ((rc = to_host(d->col_ptr, 8 * (size_t)(p + 1), colptr_h.data(), s))) return rc;
+    if (colptr_h[0] != 0) { set_error("col_ptr[0] != 0"); return SURV_E_INDEX; }
+    for (int64_t j = 0; j < p; ++j)
+      if (colptr_h[j + 1] < colptr_h[j]) { set_error("col_ptr decreases at %lld", (long long)j); return SURV_E_INDEX; }
+    nnz = colptr_h[p];
+    if ((rc = device_view(ws, W::COLPTR, d->col_ptr, 8 * (size_t)(p + 1), s, &colptr_d))) return rc;
+    if ((rc = device_view(ws, W::ROWIDX, d->row_idx, 4 * (size_t)nnz, s, &rowidx_d))) return rc;
+    if (d->values) {
+      const size_t vsz = d->dtype == SURV_F32 ? 4 : 8;
+      if ((rc = device_view(ws, W::VALUES, d->values, vsz * (size_t)nnz, s, &vals_d))) return rc;
+      if (d->dtype != prec) {
+        void* conv = nullptr;
+        if ((rc = ensure(ws, W::XD, tsz * (size_t)nnz, &conv))) return rc;
+        CUDA_TRY(survgpu::prep_convert_vec(vals_d, d->dtype, nnz, conv, prec, s));
+        ++launches;
+        vals_d = conv;
+      }
+    }
+  }
+  int64_t ld = n;
+  if (layout == SURV_DENSE) {
+    const size_t vsz = d->dtype == SURV_F32 ? 4 : 8;
+    if ((rc = device_view(ws, W::VALUES, d->values, vsz * (size_t)n * (size_t)p, s, &vals_d))) return rc;
+    const bool aligned = ((uintptr_t)vals_d % 16) == 0 && (n % 4) == 0;
+    if (d->dtype != prec || !aligned) {
+      ld = (n + 3) / 4 * 4;
+      void* conv = nullptr;
+      if ((rc = ensure(ws, W::XD, tsz * (size_t)ld * (size_t)p, &conv))) return rc;
+      CUDA_TRY(survgpu::prep_convert_dense(vals_d, d->dtype, n, p, conv, prec, ld, s));
+      ++launches;
+      vals_d = conv;
+    }
+  }
+
+  // host copies of beta and penalty factors (p values each)
+  std::vector<double> beta_h(p), pf_h(p, 1.0), pen_h(p);
+  if ((rc = to_host(beta_inout, 8 * (size_t)p, beta_h.data(), s))) return rc;
+  if (o.penalty_factor && (rc = to_host(o.penalty_factor, 8 * (size_t)p, pf_h.data(), s))) return rc;
+  for (int64_t j = 0; j < p; ++j) {
+    if (!std::isfinite(beta_h[j]) || !std::isfinite(pf_h[j]) || pf_h[j] < 0.0) {
+      set_error("non-finite beta or invalid penalty factor at %lld", (long long)j);
+      return SURV_E_NONFINITE;
+    }
+    pen_h[j] = o.lambda * pf_h[j];
+  }
+
+  // ---------------------------------------------------------- validation, K
+  void* ctrl_v = nullptr;
+  if ((rc = ensure(ws, W::CTRL, sizeof(DevCtrl), &ctrl_v))) return rc;
+  DevCtrl* ctrl = static_cast<DevCtrl*>(ctrl_v);
+  CUDA_TRY(cudaMemsetAsync(ctrl, 0, sizeof(DevCtrl), s));
+  const int32_t* time_p = static_cast<const int32_t*>(time_d);
+  const int8_t* status_p = static_cast<const int8_t*>(status_d);
+  CUDA_TRY(survgpu::prep_check_times(time_p, status_p, n, model, &ctrl->perr, s));
+  ++launches;
+  if (layout == SURV_CSC) {
+    CUDA_TRY(survgpu::prep_check_csc(static_cast<const int64_t*>(colptr_d), static_cast<const int32_t*>(rowidx_d),
+                                     vals_d, prec, p, n, &ctrl->perr, s));
+  } else {
+    CUDA_TRY(survgpu::prep_check_dense(vals_d, prec, ld, n, p, &ctrl->perr, s));
+  }
+  ++launches;
+  void* blockcnt = nullptr;
+  const int64_t nb = survgpu::prep_end_blocks(n);
+  if ((rc = ensure(ws, W::BLOCKCNT, 4 * (size_t)nb, &blockcnt))) return rc;
+  CUDA_TRY(survgpu::prep_count_ends(time_p, n, static_cast<int32_t*>(blockcnt), &ctrl->K, s));
+  launches += 2;
+  DevCtrl hc;
+  CUDA_TRY(cudaMemcpyAsync(&hc, ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if ((rc = map_prep_error(hc.perr))) return rc;
+  const int32_t K = hc.K;
+
+  // ---------------------------------------------------------- tables
+  void *gend, *dk, *ck, *Gk, *rec, *e, *eta, *w2 = nullptr, *wk0, *woff = nullptr, *dTx, *beta, *width, *pen, *slots;
+  const size_t accsz = prec == 0 ? 8 : 8;  // ff (2 floats) or double
+  if ((rc = ensure(ws, W::GEND, 4 * (size_t)K, &gend))) return rc;
+  if ((rc = ensure(ws, W::DK, 4 * (size_t)K, &dk))) return rc;
+  if ((rc = ensure(ws, W::CK, 4 * (size_t)K, &ck))) return rc;
+  if ((rc = ensure(ws, W::GK, 8 * (size_t)K, &Gk))) return rc;
+  if ((rc = ensure(ws, W::REC, accsz * (size_t)K * M, &rec))) return rc;
+  if ((rc = ensure(ws, W::E, tsz * (size_t)n, &e))) return rc;
+  if ((rc = ensure(ws, W::ETA, 8 * (size_t)n, &eta))) return rc;
+  if (model == SURV_FG && (rc = ensure(ws, W::W2, tsz * (size_t)n, &w2))) return rc;
+  if ((rc = ensure(ws, W::WK0, 4 * (size_t)(nwarps + 1), &wk0))) return rc;
+  if (layout == SURV_CSC && (rc = ensure(ws, W::WOFF, 4 * (size_t)p * (nwarps + 1), &woff))) return rc;
+  if ((rc = ensure(ws, W::DTX, 8 * (size_t)p, &dTx))) return rc;
+  if ((rc = ensure(ws, W::BETA, 8 * (size_t)p, &beta))) return rc;
+  if ((rc = ensure(ws, W::WIDTH, 8 * (size_t)p, &width))) return rc;
+  if ((rc = ensure(ws, W::PEN, 8 * (size_t)p, &pen))) return rc;
+  const size_t slot_bytes = 4 * (size_t)survgpu::kSlotWords * 2 * G;
+  if ((rc = ensure(ws, W::SLOTS, 2 * slot_bytes, &slots))) return rc;
+
+  CUDA_TRY(survgpu::prep_write_ends(time_p, n, static_cast<const int32_t*>(blockcnt), static_cast<int32_t*>(gend), s));
+  CUDA_TRY(survgpu::prep_group_stats(static_cast<int32_t*>(gend), K, status_p, static_cast<int32_t*>(dk),
+                                     static_cast<int32_t*>(ck), &ctrl->total_events, s));
+  launches += 2;
+  if (model == SURV_FG) {
+    CUDA_TRY(survgpu::prep_km(static_cast<int32_t*>(gend), static_cast<int32_t*>(ck), K, static_cast<double*>(Gk), s));
+    CUDA_TRY(survgpu::prep_w2(static_cast<int32_t*>(gend), K, status_p, static_cast<double*>(Gk), w2, prec, s));
+    launches += 2;
+  }
+  if (layout == SURV_CSC) {
+    CUDA_TRY(survgpu::prep_dtx_csc(static_cast<const int64_t*>(colptr_d), static_cast<const int32_t*>(rowidx_d),
+                                   vals_d, prec, status_p, p, static_cast<double*>(dTx), s));
+    CUDA_TRY(survgpu::prep_warp_offsets(static_cast<const int64_t*>(colptr_d), static_cast<const int32_t*>(rowidx_d),
+                                        p, n, nwarps, rows_per_warp, static_cast<int32_t*>(woff), s));
+    launches += 2;
+  } else {
+    CUDA_TRY(survgpu::prep_dtx_dense(vals_d, prec, ld, n, status_p, p, static_cast<double*>(dTx), s));
+    ++launches;
+  }
+  CUDA_TRY(survgpu::prep_warp_groups(static_cast<int32_t*>(gend), K, n, nwarps, rows_per_warp,
+                                     static_cast<int32_t*>(wk0), s));
+  ++launches;
+  CUDA_TRY(cudaMemcpyAsync(beta, beta_h.data(), 8 * (size_t)p, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(pen, pen_h.data(), 8 * (size_t)p, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(survgpu::prep_fill_f64(static_cast<double*>(width), 1.0, p, s));
+  ++launches;
+  bool any_beta = false;
+  for (double b : beta_h) any_beta |= (b != 0.0);
+  if (!any_beta) {
+    CUDA_TRY(survgpu::prep_eta_zero(prec, n, eta, e, s));
+    ++launches;
+  } else if (layout == SURV_DENSE) {
+    CUDA_TRY(survgpu::prep_eta_dense(vals_d, prec, ld, n, p, static_cast<double*>(beta), eta, e, s));
+    ++launches;
+  } else {
+    CUDA_TRY(survgpu::prep_eta_zero(prec, n, eta, e, s));
+    ++launches;
+    const size_t vsz = prec == 0 ? 4 : 8;
+    for (int64_t j = 0; j < p; ++j) {
+      if (beta_h[j] == 0.0) continue;
+      const int64_t a = colptr_h[j], b = colptr_h[j + 1];
+      const void* vj = vals_d ? static_cast<const char*>(vals_d) + vsz * (size_t)a : nullptr;
+      CUDA_TRY(survgpu::prep_eta_axpy_csc(nullptr, static_cast<const int32_t*>(rowidx_d) + a, vj, prec, j, b - a,
+                                          beta_h[j], eta, s));
+      ++launches;
+    }
+    CUDA_TRY(survgpu::prep_eta_exp(prec, n, eta, e, s));
+    ++launches;
+  }
+  CUDA_TRY(cudaMemsetAsync(slots, 0, 2 * slot_bytes, s));
+  CUDA_TRY(cudaMemcpyAsync(&hc, ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (hc.total_events <= 0) { set_error("no events"); return SURV_E_NO_EVENTS; }
+
+  // ---------------------------------------------------------- CCD kernel
+  CcdParams P;
+  std::memset(&P, 0, sizeof(P));
+  P.n = n;
+  P.ld = ld;
+  P.p = (int32_t)p;
+  P.K = K;
+  P.G = G;
+  P.wpc = wpc;
+  P.wpw = wpw;
+  P.nwarps = nwarps;
+  P.gend = static_cast<const int32_t*>(gend);
+  P.dk = static_cast<const int32_t*>(dk);
+  P.Gk = static_cast<const double*>(Gk);
+  P.wk0 = static_cast<const int32_t*>(wk0);
+  P.col_ptr = static_cast<const int64_t*>(colptr_d);
+  P.row_idx = static_cast<const int32_t*>(rowidx_d);
+  P.values = layout == SURV_CSC ? vals_d : nullptr;
+  P.woff = static_cast<const int32_t*>(woff);
+  P.X = layout == SURV_DENSE ? vals_d : nullptr;
+  P.e = e;
+  P.eta = eta;
+  P.w2 = w2;
+  P.dTx = static_cast<const double*>(dTx);
+  P.beta = static_cast<double*>(beta);
+  P.width = static_cast<double*>(width);
+  P.pen = static_cast<const double*>(pen);
+  P.rec = rec;
+  P.slot_agg = static_cast<unsigned*>(slots);
+  P.slot_part = static_cast<unsigned*>(slots) + survgpu::kSlotWords * 2 * G;
+  P.counters = ctrl->counters;
+  P.err = &ctrl->err;
+  P.out = ctrl->out;
+  P.penalty = single_j >= 0 ? 0 : o.penalty;
+  P.max_sweeps = o.max_sweeps;
+  P.tol = o.tol;
+  P.single_j = single_j;
+  P.withhold_cta = (o.flags & SURV_FLAG_TEST_STALL) ? 0 : -1;
+  P.epoch0 = 0;
+  P.timeout_ns = (uint64_t)((o.wait_limit_s > 0.0 ? o.wait_limit_s : 2.0) * 1e9);
+  struct Events {
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~Events() {
+      if (a) cudaEventDestroy(a);
+      if (b) cudaEventDestroy(b);
+    }
+  } ev;
+  CUDA_TRY(cudaEventCreate(&ev.a));
+  CUDA_TRY(cudaEventCreate(&ev.b));
+  CUDA_TRY(cudaEventRecord(ev.a, s));
+  CUDA_TRY(survgpu::launch_ccd(model, layout, prec, P, s));
+  ++launches;
+  CUDA_TRY(cudaEventRecord(ev.b, s));
+  CUDA_TRY(cudaMemcpyAsync(&hc, ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, s));
+  std::vector<double> beta_out(p);
+  CUDA_TRY(cudaMemcpyAsync(beta_out.data(), beta, 8 * (size_t)p, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  float kernel_ms = 0.f;
+  CUDA_TRY(cudaEventElapsedTime(&kernel_ms, ev.a, ev.b));
+
+  if (single_j < 0) {
+    CUDA_TRY(cudaMemcpyAsync(beta_inout, beta_out.data(), 8 * (size_t)p, cudaMemcpyDefault, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->sweeps = (int32_t)hc.out[survgpu::OUT_SWEEPS];
+    info->converged = (int32_t)hc.out[survgpu::OUT_CONVERGED];
+    int nz = 0;
+    for (double b : beta_out) nz += b != 0.0;
+    info->nnz_beta = nz;
+    info->device_error = (int32_t)hc.err;
+    info->loglik = hc.out[survgpu::OUT_LOGLIK];
+    info->objective = hc.out[survgpu::OUT_OBJECTIVE];
+    info->objective_prev = hc.out[survgpu::OUT_OBJECTIVE_PREV];
+    info->n_groups = K;
+    info->coordinate_passes = (int64_t)hc.out[survgpu::OUT_PASSES];
+    info->eta_updates = (int64_t)hc.out[survgpu::OUT_ETA_UPDATES];
+    info->kernel_launches = launches;
+    info->ccd_kernel_ms = kernel_ms;
+  }
+  if (hc.err != 0) {
+    set_error("device-side wait expired (error word 0x%x)", hc.err);
+    return SURV_E_DEVICE_TIMEOUT;
+  }
+  if (single_j >= 0) {
+    if (out_l) *out_l = hc.out[survgpu::OUT_LOGLIK];
+    if (out_g) *out_g = hc.out[survgpu::OUT_GRAD];
+    if (out_h) *out_h = hc.out[survgpu::OUT_HESS];
+    return SURV_OK;
+  }
+  return hc.out[survgpu::OUT_CONVERGED] != 0.0 ? SURV_OK : SURV_W_NOT_CONVERGED;
+}
+
+}  // namespace
+
+extern "C" {
+
+void surv_opts_default(surv_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->penalty = SURV_PEN_NONE;
+  o->precision = SURV_PREC_F32C;
+  o->lambda = 0.0;
+  o->tol = 1e-8;
+  o->max_sweeps = 1000;
+}
+
+int surv_workspace_create(surv_workspace** ws) {
+  if (!ws) { set_error("null handle pointer"); return SURV_E_INVALID; }
+  *ws = new surv_workspace();
+  return SURV_OK;
+}
+
+int surv_workspace_destroy(surv_workspace* ws) {
+  if (!ws) return SURV_OK;
+  free_all(ws);
+  delete ws;
+  return SURV_OK;
+}
+
+int surv_sort_desc(const int32_t* time, int64_t n, int32_t* perm, void* stream) {
+  g_last_error[0] = '\0';
+  if (n < 0 || n > 0x7fffffff) { set_error("bad n"); return SURV_E_INVALID; }
+  if (n == 0) return SURV_OK;
+  if (!time || !perm) { set_error("null time/perm"); return SURV_E_INVALID; }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  surv_workspace ws;
+  struct Free { surv_workspace* w; ~Free() { free_all(w); } } fr{&ws};
+  const void* tdev = nullptr;
+  int rc = device_view(&ws, surv_workspace::TIME, time, 4 * (size_t)n, s, &tdev);
+  if (rc) return rc;
+  void* work = nullptr;
+  if ((rc = ensure(&ws, surv_workspace::SORTWORK, survgpu::radix_sort_workspace(n), &work))) return rc;
+  const bool perm_dev = is_device_ptr(perm);
+  void* pdev = perm;
+  if (!perm_dev && (rc = ensure(&ws, surv_workspace::PERM, 4 * (size_t)n, &pdev))) return rc;
+  int launches = 0;
+  CUDA_TRY(survgpu::radix_sort_desc(static_cast<const int32_t*>(tdev), n, static_cast<int32_t*>(pdev), work, s,
+                                    &launches));
+  if (!perm_dev) CUDA_TRY(cudaMemcpyAsync(perm, pdev, 4 * (size_t)n, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return SURV_OK;
+}
+
+int cox_fit(const surv_data* data, const surv_opts* opts, double* beta_inout, surv_fit_info* info) {
+  return fit_common(SURV_COX, data, opts, beta_inout, info, -1, nullptr, nullptr, nullptr);
+}
+
+int fg_fit(const surv_data* data, const surv_opts* opts, double* beta_inout, surv_fit_info* info) {
+  return fit_common(SURV_FG, data, opts, beta_inout, info, -1, nullptr, nullptr, nullptr);
+}
+
+int loglik_grad_hess(const surv_data* data, int32_t model, const double* beta, int32_t j, double* loglik,
+                     double* grad, double* hess, const surv_opts* opts) {
+  if (model != SURV_COX && model != SURV_FG) { set_error("bad model"); return SURV_E_INVALID; }
+  if (j < 0) { set_error("negative j"); return SURV_E_INVALID; }
+  return fit_common(model, data, opts, const_cast<double*>(beta), nullptr, j, loglik, grad, hess);
+}
+
+int surv_groups(const int32_t* time, const int8_t* status, int64_t n, int64_t max_groups, int64_t* K_out,
+                int32_t* gend_out, int32_t* dk_out, double* Gk_out, void* stream) {
+  g_last_error[0] = '\0';
+  if (n < 0 || n > 0x7fffffff || !K_out) { set_error("bad n or null K"); return SURV_E_INVALID; }
+  *K_out = 0;
+  if (n == 0) return SURV_OK;
+  if (!time || !status) { set_error("null time/status"); return SURV_E_INVALID; }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  surv_workspace ws;
+  struct Free { surv_workspace* w; ~Free() { free_all(w); } } fr{&ws};
+  using W = surv_workspace;
+  const void *time_d = nullptr, *status_d = nullptr;
+  int rc;
+  if ((rc = device_view(&ws, W::TIME, time, 4 * (size_t)n, s, &time_d))) return rc;
+  if ((rc = device_view(&ws, W::STATUS, status, (size_t)n, s, &status_d))) return rc;
+  void *ctrl_v, *blockcnt;
+  if ((rc = ensure(&ws, W::CTRL, sizeof(DevCtrl), &ctrl_v))) return rc;
+  DevCtrl* ctrl = static_cast<DevCtrl*>(ctrl_v);
+  CUDA_TRY(cudaMemsetAsync(ctrl, 0, sizeof(DevCtrl), s));
+  const int32_t* tp = static_cast<const int32_t*>(time_d);
+  const int8_t* sp = static_cast<const int8_t*>(status_d);
+  CUDA_TRY(survgpu::prep_check_times(tp, sp, n, 1, &ctrl->perr, s));
+  if ((rc = ensure(&ws, W::BLOCKCNT, 4 * (size_t)survgpu::prep_end_blocks(n), &blockcnt))) return rc;
+  CUDA_TRY(survgpu::prep_count_ends(tp, n, static_cast<int32_t*>(blockcnt), &ctrl->K, s));
+  DevCtrl hc;
+  CUDA_TRY(cudaMemcpyAsync(&hc, ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if ((rc = map_prep_error(hc.perr))) return rc;
+  const int32_t K = hc.K;
+  *K_out = K;
+  if (!gend_out && !dk_out && !Gk_out) return SURV_OK;
+  if (K > max_groups) { set_error("K=%d exceeds max_groups", K); return SURV_E_INVALID; }
+  void *gend, *dk, *ck, *Gk;
+  if ((rc = ensure(&ws, W::GEND, 4 * (size_t)K, &gend))) return rc;
+  if ((rc = ensure(&ws, W::DK, 4 * (size_t)K, &dk))) return rc;
+  if ((rc = ensure(&ws, W::CK, 4 * (size_t)K, &ck))) return rc;
+  if ((rc = ensure(&ws, W::GK, 8 * (size_t)K, &Gk))) return rc;
+  CUDA_TRY(survgpu::prep_write_ends(tp, n, static_cast<const int32_t*>(blockcnt), static_cast<int32_t*>(gend), s));
+  CUDA_TRY(survgpu::prep_group_stats(static_cast<int32_t*>(gend), K, sp, static_cast<int32_t*>(dk),
+                                     static_cast<int32_t*>(ck), &ctrl->total_events, s));
+  CUDA_TRY(survgpu::prep_km(static_cast<int32_t*>(gend), static_cast<int32_t*>(ck), K, static_cast<double*>(Gk), s));
+  if (gend_out) CUDA_TRY(cudaMemcpyAsync(gend_out, gend, 4 * (size_t)K, cudaMemcpyDefault, s));
+  if (dk_out) CUDA_TRY(cudaMemcpyAsync(dk_out, dk, 4 * (size_t)K, cudaMemcpyDefault, s));
+  if (Gk_out) CUDA_TRY(cudaMemcpyAsync(Gk_out, Gk, 8 * (size_t)K, cudaMemcpyDefault, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return SURV_OK;
+}
+
+const char* surv_strerror(int code) {
+  switch (code) {
+    case SURV_OK: return "ok";
+    case SURV_W_NOT_CONVERGED: return "not converged";
+    case SURV_E_INVALID: return "invalid argument";
+    case SURV_E_UNSORTED: return "time not sorted in decreasing order";
+    case SURV_E_STATUS: return "invalid status code";
+    case SURV_E_NONFINITE: return "non-finite value";
+    case SURV_E_NO_EVENTS: return "no events";
+    case SURV_E_CUDA: return "CUDA error";
+    case SURV_E_DEVICE_TIMEOUT: return "device wait timed out";
+    case SURV_E_NOMEM: return "out of device memory";
+    case SURV_E_INDEX: return "malformed CSC indices";
+    default: return "unknown code";
+  }
+}
+
+const char* surv_last_error(void) { return g_last_error; }
+
+int surv_version(void) { return 100; }
+
+}  // extern "C"

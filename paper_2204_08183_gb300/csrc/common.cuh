@@ -1,0 +1,196 @@
+// Device helpers shared by the survgpu kernels (sm_103a).
+//
+// * float-float ("ff") arithmetic: an unevaluated sum hi + lo of two floats,
+//   built from Knuth's TwoSum and the FMA form of Dekker's TwoProd.  It gives
+//   about 44-48 significant bits with FP32 instructions only; GB300's FP64
+//   pipe is far too slow for per-element or per-group use.  The __f*_rn
+//   intrinsics keep the compiler from contracting the error terms into FMAs.
+// * acquire/release flag access and a bounded wait used by the grid-wide
+//   exchange of the persistent CCD kernel.  Every wait gives up after a
+//   wall-clock limit read from %globaltimer and raises an error word instead
+//   of spinning forever.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace survgpu {
+
+// ------------------------------------------------------------------ ff type
+struct ff {
+  float hi, lo;
+};
+
+__device__ __forceinline__ ff ff_zero() { return {0.f, 0.f}; }
+
+__device__ __forceinline__ ff two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, err};
+}
+
+// requires |a| >= |b| (or a == 0)
+__device__ __forceinline__ ff fast_two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float err = __fsub_rn(b, __fsub_rn(s, a));
+  return {s, err};
+}
+
+// accurate ff + ff (two TwoSums, renormalised)
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  ff s = two_sum(a.hi, b.hi);
+  ff t = two_sum(a.lo, b.lo);
+  s.lo = __fadd_rn(s.lo, t.hi);
+  s = fast_two_sum(s.hi, s.lo);
+  s.lo = __fadd_rn(s.lo, t.lo);
+  return fast_two_sum(s.hi, s.lo);
+}
+
+__device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
+
+// ff + float
+__device__ __forceinline__ ff ff_add_f(ff a, float b) {
+  ff s = two_sum(a.hi, b);
+  s.lo = __fadd_rn(s.lo, a.lo);
+  return fast_two_sum(s.hi, s.lo);
+}
+
+// ff * float (exact product of the leading parts via FMA)
+__device__ __forceinline__ ff ff_mul_f(ff a, float b) {
+  float p = __fmul_rn(a.hi, b);
+  float e = fmaf(a.hi, b, -p);
+  e = fmaf(a.lo, b, e);
+  return fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  float p = __fmul_rn(a.hi, b.hi);
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return fast_two_sum(p, e);
+}
+
+// a / b with two correction steps (long division on the leading parts)
+__device__ __forceinline__ ff ff_div(ff a, ff b) {
+  float q1 = __fdiv_rn(a.hi, b.hi);
+  ff r = ff_sub(a, ff_mul_f(b, q1));
+  float q2 = __fdiv_rn(r.hi, b.hi);
+  r = ff_sub(r, ff_mul_f(b, q2));
+  float q3 = __fdiv_rn(r.hi, b.hi);
+  ff q = fast_two_sum(q1, q2);
+  return ff_add_f(q, q3);
+}
+
+__device__ __forceinline__ double ff_to_d(ff a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ ff d_to_ff(double d) {
+  float hi = (float)d;
+  float lo = (float)(d - (double)hi);
+  return {hi, lo};
+}
+
+// ------------------------------------------------------------ accumulators
+// Acc<float> is ff, Acc<double> is double: one code path for both precision
+// modes of the kernels.
+template <typename T> struct AccOf;
+template <> struct AccOf<float> { using type = ff; };
+template <> struct AccOf<double> { using type = double; };
+
+__device__ __forceinline__ void acc_zero(ff& a) { a = ff_zero(); }
+__device__ __forceinline__ void acc_zero(double& a) { a = 0.0; }
+__device__ __forceinline__ ff acc_add(ff a, ff b) { return ff_add(a, b); }
+__device__ __forceinline__ double acc_add(double a, double b) { return a + b; }
+__device__ __forceinline__ ff acc_add_v(ff a, float v) { return ff_add_f(a, v); }
+__device__ __forceinline__ double acc_add_v(double a, double v) { return a + v; }
+__device__ __forceinline__ double acc_to_d(ff a) { return ff_to_d(a); }
+__device__ __forceinline__ double acc_to_d(double a) { return a; }
+__device__ __forceinline__ ff acc_neg(ff a) { return ff_neg(a); }
+__device__ __forceinline__ double acc_neg(double a) { return -a; }
+
+__device__ __forceinline__ ff shfl_down(ff a, int d) {
+  return {__shfl_down_sync(0xffffffffu, a.hi, d), __shfl_down_sync(0xffffffffu, a.lo, d)};
+}
+__device__ __forceinline__ double shfl_down(double a, int d) { return __shfl_down_sync(0xffffffffu, a, d); }
+__device__ __forceinline__ ff shfl_up(ff a, int d) {
+  return {__shfl_up_sync(0xffffffffu, a.hi, d), __shfl_up_sync(0xffffffffu, a.lo, d)};
+}
+__device__ __forceinline__ double shfl_up(double a, int d) { return __shfl_up_sync(0xffffffffu, a, d); }
+__device__ __forceinline__ ff shfl_idx(ff a, int s) {
+  return {__shfl_sync(0xffffffffu, a.hi, s), __shfl_sync(0xffffffffu, a.lo, s)};
+}
+__device__ __forceinline__ double shfl_idx(double a, int s) { return __shfl_sync(0xffffffffu, a, s); }
+
+// Fixed-shape tree reduction over the 32 lanes (result valid in lane 0 and
+// broadcast to all lanes).  The order of additions does not depend on timing.
+template <typename A>
+__device__ __forceinline__ A warp_sum(A v) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) v = acc_add(v, shfl_down(v, d));
+  return shfl_idx(v, 0);
+}
+
+// Inclusive scan over lanes (Hillis-Steele, fixed shape).
+template <typename A>
+__device__ __forceinline__ A warp_inclusive_scan(A v, int lane) {
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    A u = shfl_up(v, d);
+    if (lane >= d) v = acc_add(v, u);
+  }
+  return v;
+}
+
+// ---------------------------------------------------------- flags / waits
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_volatile(const unsigned* p) {
+  return *reinterpret_cast<const volatile unsigned*>(p);
+}
+
+// Device error bits (also reported to the host in surv_fit_info).
+enum : unsigned {
+  DEV_ERR_TIMEOUT = 1u,      // a grid exchange wait gave up
+  DEV_ERR_ABORT = 2u,        // a test-only abort request was honoured
+};
+
+// Wait (one warp) until the epoch word of every slot 0..count-1 equals or
+// exceeds `epoch`.  Slots are `stride` words apart, the epoch sits at word
+// `eoff` of each slot.  Gives up after `limit_ns` (sets DEV_ERR_TIMEOUT) or
+// as soon as another block has raised an error.  Returns true on success
+// (same value in all lanes).
+__device__ __forceinline__ bool warp_wait_epochs(const unsigned* slots, int count, int stride, int eoff,
+                                                 unsigned epoch, unsigned* err, uint64_t limit_ns) {
+  const int lane = threadIdx.x & 31;
+  bool ok = true;
+  uint64_t t0 = 0;
+  bool timed = false;
+  for (int q = lane; q < count; q += 32) {
+    const unsigned* f = slots + (size_t)q * stride + eoff;
+    while (ld_acquire(f) < epoch) {
+      if (ld_volatile(err) != 0u) { ok = false; break; }
+      if (!timed) { t0 = global_ns(); timed = true; }
+      if (global_ns() - t0 > limit_ns) {
+        atomicOr(err, DEV_ERR_TIMEOUT);
+        ok = false;
+        break;
+      }
+    }
+    if (!ok) break;
+  }
+  return __all_sync(0xffffffffu, ok);
+}
+
+}  // namespace survgpu

@@ -1,0 +1,132 @@
+// Internal declarations shared by the survgpu translation units (not part of
+// the public C ABI).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace survgpu {
+
+constexpr int kMaxWarpsPerCta = 32;            // persistent CCD kernel: up to 1024 threads
+constexpr int kSlotWords = 32;                 // one 128-byte exchange slot per CTA
+
+// Prep error bits (host maps them to SURV_E_* codes).
+enum : unsigned {
+  PREP_UNSORTED = 1u,
+  PREP_STATUS = 2u,
+  PREP_NONFINITE = 4u,
+  PREP_INDEX = 8u,
+};
+
+// Parameters of the persistent CCD kernel (passed as a __grid_constant__).
+struct CcdParams {
+  int64_t n;          // subjects
+  int64_t ld;         // leading dimension of dense X (>= n, multiple of 4)
+  int32_t p;          // covariates
+  int32_t K;          // tie groups
+  int32_t G;          // CTAs (co-resident)
+  int32_t wpc;        // warps per CTA (blockDim.x = 32 * wpc)
+  int32_t wpw;        // 32-row words per warp
+  int32_t nwarps;     // G * wpc
+
+  const int32_t* gend;   // [K] group end positions
+  const int32_t* dk;     // [K] events per group (Cox) / primary events (FG)
+  const double* Gk;      // [K] Kaplan-Meier censoring survival at t_k (FG)
+  const int32_t* wk0;    // [nwarps+1] first group index whose end is in warp w
+
+  const int64_t* col_ptr;  // CSC
+  const int32_t* row_idx;
+  const void* values;      // CSC values (T) or null for indicators
+  const int32_t* woff;     // [p][nwarps+1] entry offset of warp boundaries
+  const void* X;           // dense column-major (T), leading dimension ld
+
+  void* e;               // [n] exp(eta) (T)
+  void* eta;             // [n] eta: float2 (float-float) or double
+  const void* w2;        // [n] I(status=2)/G(y_i) (T), FG only
+  const double* dTx;     // [p] delta^T X_j
+  double* beta;          // [p] coefficients (written by CTA 0)
+  double* width;         // [p] trust-region half-widths (written by CTA 0)
+  const double* pen;     // [p] lambda * penalty_factor_j
+  void* rec;             // [K][M] accumulators: prefix at group ends, warp-relative
+
+  unsigned* slot_agg;    // [2][G][kSlotWords] CTA aggregates, by epoch parity
+  unsigned* slot_part;   // [2][G][kSlotWords] CTA partial sums, by epoch parity
+  unsigned* counters;    // [2] arrival counters of the two exchanges (zeroed per launch)
+  unsigned* err;         // device error word
+  double* out;           // results, see OutIndex
+
+  int32_t penalty;
+  int32_t max_sweeps;
+  double tol;
+  int32_t single_j;      // >= 0: evaluate coordinate single_j once and stop
+  int32_t withhold_cta;  // test knob: this CTA never publishes (-1 = off)
+  unsigned epoch0;       // unused (counters restart at 0 every launch)
+  uint64_t timeout_ns;   // bound on every grid-exchange wait
+};
+
+enum OutIndex : int {
+  OUT_LOGLIK = 0,
+  OUT_OBJECTIVE = 1,
+  OUT_OBJECTIVE_PREV = 2,
+  OUT_SWEEPS = 3,
+  OUT_CONVERGED = 4,
+  OUT_ETA_UPDATES = 5,
+  OUT_GRAD = 6,
+  OUT_HESS = 7,
+  OUT_PASSES = 8,
+  OUT_EPOCH_END = 9,
+  OUT_COUNT = 16,
+};
+
+// Launch the persistent CCD kernel (cooperative launch).  model 0 Cox / 1 FG,
+// layout 0 CSC / 1 dense, prec 0 float-float / 1 double.
+cudaError_t launch_ccd(int model, int layout, int prec, const CcdParams& P, cudaStream_t s);
+// Co-resident CTAs and warps per CTA of the CCD kernel for this configuration.
+cudaError_t ccd_grid_size(int model, int layout, int prec, int* G, int* wpc);
+
+// ---- prep kernels (prep.cu) --------------------------------------------
+cudaError_t prep_check_times(const int32_t* time, const int8_t* status, int64_t n, int model,
+                             unsigned* perr, cudaStream_t s);
+cudaError_t prep_check_csc(const int64_t* col_ptr, const int32_t* row_idx, const void* values, int prec,
+                           int64_t p, int64_t n, unsigned* perr, cudaStream_t s);
+cudaError_t prep_check_dense(const void* X, int prec, int64_t ld, int64_t n, int64_t p, unsigned* perr,
+                             cudaStream_t s);
+cudaError_t prep_check_finite_f64(const double* v, int64_t count, unsigned* perr, cudaStream_t s);
+// Count tie groups: writes per-block counts into blockcnt [nblocks] and K into *K_dev.
+int64_t prep_end_blocks(int64_t n);
+cudaError_t prep_count_ends(const int32_t* time, int64_t n, int32_t* blockcnt, int32_t* K_dev, cudaStream_t s);
+cudaError_t prep_write_ends(const int32_t* time, int64_t n, const int32_t* blockoff, int32_t* gend, cudaStream_t s);
+cudaError_t prep_group_stats(const int32_t* gend, int32_t K, const int8_t* status, int32_t* dk, int32_t* ck,
+                             int32_t* total_events, cudaStream_t s);
+cudaError_t prep_km(const int32_t* gend, const int32_t* ck, int32_t K, double* Gk, cudaStream_t s);
+cudaError_t prep_w2(const int32_t* gend, int32_t K, const int8_t* status, const double* Gk, void* w2, int prec,
+                    cudaStream_t s);
+cudaError_t prep_dtx_csc(const int64_t* col_ptr, const int32_t* row_idx, const void* values, int prec,
+                         const int8_t* status, int64_t p, double* dTx, cudaStream_t s);
+cudaError_t prep_dtx_dense(const void* X, int prec, int64_t ld, int64_t n, const int8_t* status, int64_t p,
+                           double* dTx, cudaStream_t s);
+cudaError_t prep_warp_groups(const int32_t* gend, int32_t K, int64_t n, int32_t nwarps, int64_t rows_per_warp,
+                             int32_t* wk0, cudaStream_t s);
+cudaError_t prep_warp_offsets(const int64_t* col_ptr, const int32_t* row_idx, int64_t p, int64_t n,
+                              int32_t nwarps, int64_t rows_per_warp, int32_t* woff, cudaStream_t s);
+cudaError_t prep_eta_dense(const void* X, int prec, int64_t ld, int64_t n, int64_t p, const double* beta,
+                           void* eta, void* e, cudaStream_t s);
+cudaError_t prep_eta_zero(int prec, int64_t n, void* eta, void* e, cudaStream_t s);
+cudaError_t prep_eta_axpy_csc(const int64_t* col_ptr, const int32_t* row_idx, const void* values, int prec,
+                              int64_t j, int64_t nnz_j, double delta, void* eta, cudaStream_t s);
+cudaError_t prep_eta_exp(int prec, int64_t n, const void* eta, void* e, cudaStream_t s);
+cudaError_t prep_fill_f64(double* v, double value, int64_t count, cudaStream_t s);
+// Convert / pad a dense matrix into the working precision with leading
+// dimension ld (src column-major, leading dimension n).
+cudaError_t prep_convert_dense(const void* src, int src_dtype, int64_t n, int64_t p, void* dst, int prec,
+                               int64_t ld, cudaStream_t s);
+cudaError_t prep_convert_vec(const void* src, int src_dtype, int64_t count, void* dst, int prec, cudaStream_t s);
+
+// ---- sort (sort.cu) -----------------------------------------------------
+// Workspace bytes needed by radix_sort_desc for n elements.
+size_t radix_sort_workspace(int64_t n);
+cudaError_t radix_sort_desc(const int32_t* time, int64_t n, int32_t* perm, void* work, cudaStream_t s,
+                            int* launches);
+
+}  // namespace survgpu

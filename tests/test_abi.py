@@ -1,0 +1,94 @@
+"""C ABI checks that need no GPU: the library builds and loads, exports every
+function the header declares, and the ctypes mirrors of the structs have the
+same sizes and field offsets as the C compiler gives them."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2204_08183_gb300 import binding, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "survgpu.h")
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    return build.build()
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*([a-z_0-9]+)\s*\(", text, flags=re.M)
+    return [n for n in names if n not in ("if", "while", "return")]
+
+
+def test_header_functions_are_exported(libpath):
+    declared = _declared_functions()
+    assert "cox_fit" in declared and "fg_fit" in declared and "loglik_grad_hess" in declared
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r" T (\w+)$", out, flags=re.M))
+    missing = [n for n in declared if n not in exported]
+    assert not missing, missing
+    assert sorted(declared) == sorted(binding.EXPORTS)
+
+
+def test_library_loads_without_gpu(libpath):
+    lib = C.CDLL(libpath)
+    for name in binding.EXPORTS:
+        assert hasattr(lib, name)
+    lib.surv_version.restype = C.c_int
+    assert lib.surv_version() >= 100
+    lib.surv_strerror.restype = C.c_char_p
+    assert lib.surv_strerror(-2) == b"time not sorted in decreasing order"
+
+
+def test_struct_layouts_match_c(tmp_path):
+    src = tmp_path / "layout.c"
+    src.write_text(r'''
+#include <stddef.h>
+#include <stdio.h>
+#include "survgpu.h"
+#define F(S, m) printf(#S "." #m " %zu\n", offsetof(S, m))
+int main(void) {
+  printf("surv_data %zu\n", sizeof(surv_data));
+  printf("surv_opts %zu\n", sizeof(surv_opts));
+  printf("surv_fit_info %zu\n", sizeof(surv_fit_info));
+  F(surv_data, n); F(surv_data, p); F(surv_data, time); F(surv_data, status); F(surv_data, layout);
+  F(surv_data, dtype); F(surv_data, col_ptr); F(surv_data, row_idx); F(surv_data, values);
+  F(surv_opts, penalty); F(surv_opts, precision); F(surv_opts, lambda); F(surv_opts, penalty_factor);
+  F(surv_opts, tol); F(surv_opts, max_sweeps); F(surv_opts, flags); F(surv_opts, wait_limit_s);
+  F(surv_opts, stream); F(surv_opts, workspace);
+  F(surv_fit_info, sweeps); F(surv_fit_info, converged); F(surv_fit_info, nnz_beta);
+  F(surv_fit_info, device_error); F(surv_fit_info, loglik); F(surv_fit_info, objective);
+  F(surv_fit_info, objective_prev); F(surv_fit_info, n_groups); F(surv_fit_info, coordinate_passes);
+  F(surv_fit_info, eta_updates); F(surv_fit_info, kernel_launches); F(surv_fit_info, ccd_kernel_ms);
+  return 0;
+}
+''')
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    c = dict(line.split() for line in out if line.strip())
+    structs = {"surv_data": binding.surv_data, "surv_opts": binding.surv_opts,
+               "surv_fit_info": binding.surv_fit_info}
+    for name, cls in structs.items():
+        assert int(c[name]) == C.sizeof(cls), name
+    for key, off in c.items():
+        if "." not in key:
+            continue
+        sname, field = key.split(".")
+        field = "lambda_" if field == "lambda" else field
+        assert getattr(structs[sname], field).offset == int(off), key
+
+
+def test_product_path_does_not_import_oracle():
+    pkg = os.path.join(ROOT, "paper_2204_08183_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle", text, flags=re.M), f

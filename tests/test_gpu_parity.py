@@ -1,0 +1,229 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Integer work (sort permutation, tie-group ends, event counts) must match
+bit for bit; the Kaplan-Meier product runs in the same order in FP64 and
+must match bit for bit too.  Floating results follow the tolerances derived
+in the design notes: the FP32-compensated mode stores e = exp(eta) in FP32
+(relative error ~1e-7 per term) and accumulates in float-float, so
+l is within 1e-6 relative and l', l'' within 1e-6 of the scale
+sum_k d_k max|x|^m; the FP64 mode is held to 1e-10.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2204_08183_gb300 import binding, synth
+
+from gpu_util import oracle_X, small_csc, survdata
+
+pytestmark = pytest.mark.gpu
+
+
+def _tol(prec):
+    return 1e-6 if prec == "f32c" else 1e-10
+
+
+def _check_lgh(d, model, beta, j, prec, where="device"):
+    sd = survdata(d, where)
+    l, g, h = binding.loglik_grad_hess(sd, model, np.asarray(beta, np.float64), j, precision=prec)
+    X = oracle_X(d)
+    st = d["status"] if model == "fg" else np.where(d["status"] == 2, 0, d["status"]).astype(np.int8)
+    lo, go, ho = oracle.model_terms(model, d["time"], st, X, beta, j)
+    D = max(1, int((st == 1).sum()))
+    xm = float(np.abs(oracle.column(X, j)).max()) if len(d["time"]) else 1.0
+    tol = _tol(prec)
+    assert abs(l - lo) <= tol * max(abs(lo), 1.0), (l, lo)
+    assert abs(g - go) <= tol * D * max(xm, 1e-300) + tol * abs(go), (g, go)
+    assert abs(h - ho) <= tol * D * max(xm * xm, 1e-300) + tol * abs(ho), (h, ho)
+    return (l, g, h), (lo, go, ho)
+
+
+# ------------------------------------------------------------ integer parity
+@pytest.mark.parametrize("n", [1, 7, 1000, 123457, 2_000_001])
+def test_sort_desc_bit_exact(lib, n):
+    rng = np.random.default_rng(n)
+    t = rng.integers(-50, 50 if n < 1000 else 3650, size=n).astype(np.int32)
+    if n > 10:
+        t[:5] = [np.iinfo(np.int32).min, np.iinfo(np.int32).max, 0, -1, 1]
+    perm = binding.surv_sort_desc(t)
+    assert np.array_equal(np.asarray(perm), oracle.sort_desc(t).astype(np.int32))
+    import torch
+    permd = binding.surv_sort_desc(torch.from_numpy(t).cuda())
+    assert np.array_equal(permd.cpu().numpy(), oracle.sort_desc(t).astype(np.int32))
+
+
+@pytest.mark.parametrize("n,n_times", [(1, 1), (5, 1), (1000, 1000), (1000, 37), (3_000_017, 3650)])
+def test_groups_bit_exact(lib, n, n_times):
+    rng = np.random.default_rng(n + n_times)
+    t = np.sort(rng.integers(1, n_times + 1, size=n))[::-1].astype(np.int32)
+    st = rng.choice(np.array([0, 1, 2], np.int8), size=n, p=[0.4, 0.35, 0.25])
+    gend, dk, Gk = binding.surv_groups(t, st)
+    og = oracle.tie_groups(t)
+    assert np.array_equal(gend, og.astype(np.int32))
+    assert np.array_equal(dk, oracle.group_counts(og, st, 1).astype(np.int32))
+    assert np.array_equal(Gk, oracle.km_censoring_groups(t, st, og))   # same order of FP64 products
+
+
+# ------------------------------------------------------------ one pass
+@pytest.mark.parametrize("prec", ["f32c", "f64"])
+@pytest.mark.parametrize("model", ["cox", "fg"])
+@pytest.mark.parametrize("n,n_times", [(1, 1), (2, 2), (33, 4), (1000, 1000), (4099, 60), (20011, 365)])
+def test_lgh_dense_small(lib, prec, model, n, n_times):
+    d = synth.cohort_small(n, 3, seed=n, n_times=n_times, censor_frac=0.3,
+                           competing_frac=0.25 if model == "fg" else 0.0)
+    st = d["status"].copy()
+    st[0] = 1  # at least one event
+    d["status"] = st
+    for j in range(3):
+        _check_lgh(d, model, d["beta"], j, prec)
+
+
+@pytest.mark.parametrize("prec", ["f32c", "f64"])
+@pytest.mark.parametrize("model", ["cox", "fg"])
+@pytest.mark.parametrize("binary", [False, True])
+@pytest.mark.parametrize("n,n_times", [(517, 30), (40_003, 400), (300_007, 3650)])
+def test_lgh_csc(lib, prec, model, binary, n, n_times):
+    d = small_csc(n, 4, seed=n + binary, density=0.05, n_times=n_times,
+                  competing=0.25 if model == "fg" else 0.0, binary=binary,
+                  dtype=np.float32 if prec == "f32c" else np.float64)
+    for j in range(4):
+        _check_lgh(d, model, d["beta"] * 0.5, j, prec)
+
+
+@pytest.mark.parametrize("model", ["cox", "fg"])
+def test_lgh_many_tiles_per_warp(lib, model):
+    # > 5e6 rows: every warp of the grid streams several 1024-row tiles, and
+    # n is not a multiple of 4 (ragged tail).
+    n = 5_300_003
+    if model == "cox":
+        d = synth.cohort_cox_sparse(n, 3, seed=11, density=0.05, n_true=2, grid=3650)
+        d["values"] = None
+        beta = np.array([0.1, -0.2, 0.05])
+    else:
+        d = synth.cohort_fg_dense(n, 2, seed=12, grid=1000, n_true=2)
+        beta = np.array([0.2, -0.1])
+    for j in range(d["p"] if "p" in d else 2):
+        _check_lgh(d, model, beta, j, "f32c")
+
+
+def test_lgh_edge_cases(lib):
+    X = np.asfortranarray(np.array([[0.5], [-1.0], [2.0], [0.0]]))
+    cases = [
+        # all tied, one event
+        (np.array([3, 3, 3, 3], np.int32), np.array([0, 1, 0, 0], np.int8)),
+        # no ties, all events
+        (np.array([9, 7, 5, 1], np.int32), np.array([1, 1, 1, 1], np.int8)),
+        # all censored except the last
+        (np.array([9, 7, 5, 1], np.int32), np.array([0, 0, 0, 1], np.int8)),
+        # all censored except the first (risk set of one)
+        (np.array([9, 7, 5, 1], np.int32), np.array([1, 0, 0, 0], np.int8)),
+    ]
+    for t, st in cases:
+        d = {"time": t, "status": st, "X": X, "layout": "dense"}
+        for prec in ["f32c", "f64"]:
+            for b in [0.0, 0.7]:
+                _check_lgh(d, "cox", [b], 0, prec)
+                _check_lgh(d, "fg", [b], 0, prec)
+
+
+def test_zero_column_has_zero_gradient(lib):
+    d = synth.cohort_small(300, 2, seed=3, n_times=20)
+    d["X"][:, 1] = 0.0
+    sd = survdata(d)
+    _, g, h = binding.loglik_grad_hess(sd, "cox", d["beta"], 1)
+    assert g == 0.0 and h == 0.0
+
+
+def test_host_and_device_buffers_agree(lib):
+    d = small_csc(20_000, 3, seed=4, density=0.1, n_times=200)
+    a = binding.loglik_grad_hess(survdata(d, "device"), "cox", d["beta"], 2)
+    b = binding.loglik_grad_hess(survdata(d, "host"), "cox", d["beta"], 2)
+    assert a == b
+
+
+def test_deterministic(lib):
+    d = small_csc(200_000, 3, seed=5, density=0.05, n_times=3000)
+    sd = survdata(d)
+    r = [binding.loglik_grad_hess(sd, "cox", d["beta"], 1) for _ in range(3)]
+    assert r[0] == r[1] == r[2]
+    f1 = binding.cox_fit(sd, penalty="l1", lam=5.0, tol=1e-10)
+    f2 = binding.cox_fit(sd, penalty="l1", lam=5.0, tol=1e-10)
+    assert np.array_equal(f1[0], f2[0]) and f1[1]["sweeps"] == f2[1]["sweeps"]
+
+
+# ------------------------------------------------------------ full fits
+def _fit_check(model, d, penalty, lam, prec, beta_tol=1e-5, tol=1e-10, where="device"):
+    sd = survdata(d, where)
+    fn = binding.cox_fit if model == "cox" else binding.fg_fit
+    beta, info, rc = fn(sd, penalty=penalty, lam=lam, tol=tol, max_sweeps=500, precision=prec)
+    X = oracle_X(d)
+    st = d["status"] if model == "fg" else np.where(d["status"] == 2, 0, d["status"]).astype(np.int8)
+    ref = oracle.ccd_fit(model, d["time"], st, X, penalty, lam, tol=tol, max_sweeps=500)
+    assert rc == 0 and info["converged"] == 1 and ref["converged"]
+    np.testing.assert_allclose(beta, ref["beta"], atol=beta_tol, rtol=0)
+    assert abs(info["loglik"] - ref["loglik"]) <= 1e-6 * abs(ref["loglik"])
+    # Near tol ~ 1e-10 the relative objective change reaches the FP32 rounding
+    # floor of e = exp(eta) (~1e-11), so the FP32-mode stopping sweep may land
+    # a little later than the FP64 oracle's; the iterates themselves must
+    # agree: same number of sweeps on the oracle side, tol = 0.
+    assert abs(info["sweeps"] - ref["sweeps"]) <= (1 if prec == "f64" else 3)
+    same = oracle.ccd_fit(model, d["time"], st, X, penalty, lam, tol=0.0, max_sweeps=info["sweeps"])
+    np.testing.assert_allclose(beta, same["beta"], atol=beta_tol, rtol=0)
+    # zeros of an L1 fit are exact on both sides
+    if penalty == "l1":
+        assert np.array_equal(beta == 0.0, ref["beta"] == 0.0)
+    return beta, info, ref
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32c"])
+def test_fit_dense_cox_l2_config1_shape(lib, prec):
+    # N = 10,000 subjects, p = 10 dense N(0,1) covariates, 365-day grid,
+    # ~30% censoring, L2 lambda = 1, relative-change tolerance 1e-8.
+    d = synth.cohort_cox_dense(10_000, 10, seed=1, n_true=5, beta_sd=0.5, censor_frac=0.3, grid=365)
+    _fit_check("cox", d, "l2", 1.0, prec, tol=1e-8)
+
+
+@pytest.mark.parametrize("prec", ["f32c", "f64"])
+def test_fit_csc_cox_l1(lib, prec):
+    d = synth.cohort_cox_sparse(60_000, 20, seed=2, density=0.05, n_true=4, laplace_scale=0.5, grid=3650)
+    if prec == "f64":
+        d["values"] = d["values"].astype(np.float64)
+    lmax = oracle.lambda_max("cox", d["time"], d["status"], oracle_X(d))
+    _fit_check("cox", d, "l1", 0.2 * lmax, prec)
+
+
+@pytest.mark.parametrize("prec", ["f32c", "f64"])
+def test_fit_fg_dense_l2(lib, prec):
+    d = synth.cohort_fg_dense(30_000, 6, seed=3, grid=1000, n_true=4, dtype=np.float32 if prec == "f32c" else np.float64)
+    _fit_check("fg", d, "l2", 10.0, prec)
+
+
+def test_fit_fg_csc_l1_host_buffers(lib):
+    d = small_csc(25_000, 8, seed=6, density=0.1, n_times=500, competing=0.25)
+    lmax = oracle.lambda_max("fg", d["time"], d["status"], oracle_X(d))
+    _fit_check("fg", d, "l1", 0.3 * lmax, "f32c", where="host")
+
+
+def test_fit_unpenalised_and_warm_start(lib):
+    d = synth.cohort_cox_dense(5_000, 4, seed=7, n_true=3, grid=200)
+    sd = survdata(d)
+    b0 = np.array([0.1, -0.1, 0.2, 0.0])
+    beta, info, rc = binding.cox_fit(sd, beta=b0.copy(), penalty="none", tol=1e-12, max_sweeps=300)
+    ref = oracle.ccd_fit("cox", d["time"], d["status"], d["X"], "none", 0.0, tol=1e-12, max_sweeps=300, beta0=b0)
+    np.testing.assert_allclose(beta, ref["beta"], atol=1e-6)
+
+
+def test_lambda_max_gives_zero(lib):
+    d = synth.cohort_cox_sparse(50_000, 12, seed=8, density=0.05, n_true=3, grid=1000)
+    lmax = oracle.lambda_max("cox", d["time"], d["status"], oracle_X(d))
+    beta, info, rc = binding.cox_fit(survdata(d), penalty="l1", lam=lmax * 1.001, tol=1e-10)
+    assert np.all(beta == 0.0) and info["eta_updates"] == 0
+
+
+def test_max_sweeps_reports_not_converged(lib):
+    d = synth.cohort_cox_dense(3_000, 5, seed=9, n_true=4, grid=100)
+    beta, info, rc = binding.cox_fit(survdata(d), penalty="l2", lam=1.0, tol=0.0, max_sweeps=3)
+    assert rc == binding.SURV_W_NOT_CONVERGED and info["sweeps"] == 3 and info["converged"] == 0
+    ref = oracle.ccd_fit("cox", d["time"], d["status"], d["X"], "l2", 1.0, tol=0.0, max_sweeps=3)
+    np.testing.assert_allclose(beta, ref["beta"], atol=1e-7)
+    assert info["coordinate_passes"] == 3 * 5 + 1
