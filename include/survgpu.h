@@ -135,6 +135,11 @@ typedef struct surv_fit_info {
   int64_t kernel_launches;       /* CUDA kernels launched by this call            */
   double ccd_kernel_ms;          /* device time of the CCD kernel (CUDA events on
                                     the call's stream)                            */
+  double phase_ms[6];            /* diagnostics, summed over the fit: CTA 0's
+                                    time in the row pass, exchange 1, group-end
+                                    transform, exchange 2 + Newton step, eta
+                                    update; [5] = largest row-pass total of any
+                                    CTA                                           */
 } surv_fit_info;
 
 /* ---- entry points ------------------------------------------------------ */

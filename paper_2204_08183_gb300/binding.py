@@ -61,10 +61,13 @@ class surv_fit_info(C.Structure):
     _fields_ = [("sweeps", C.c_int32), ("converged", C.c_int32), ("nnz_beta", C.c_int32),
                 ("device_error", C.c_int32), ("loglik", C.c_double), ("objective", C.c_double),
                 ("objective_prev", C.c_double), ("n_groups", C.c_int64), ("coordinate_passes", C.c_int64),
-                ("eta_updates", C.c_int64), ("kernel_launches", C.c_int64), ("ccd_kernel_ms", C.c_double)]
+                ("eta_updates", C.c_int64), ("kernel_launches", C.c_int64), ("ccd_kernel_ms", C.c_double),
+                ("phase_ms", C.c_double * 6)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["phase_ms"] = list(self.phase_ms)
+        return d
 
 
 _lib = None

@@ -18,7 +18,7 @@ struct surv_workspace {
     size_t cap = 0;
   };
   enum Id {
-    TIME, STATUS, COLPTR, ROWIDX, VALUES, XD, E, ETA, W2, GEND, DK, CK, GK, WK0, WOFF, DTX, BETA, WIDTH, PEN, REC,
+    TIME, STATUS, COLPTR, ROWIDX, VALUES, XD, E, ETA, W2, GEND, DK, CK, GK, GKFF, WK0, WOFF, DTX, BETA, WIDTH, PEN, REC,
     SLOTS, CTRL, BLOCKCNT, SORTWORK, PERM, PF, NBUF
   };
   int device = -1;
@@ -46,6 +46,7 @@ struct DevCtrl {
   unsigned counters[2];
   unsigned pad[2];
   double out[survgpu::OUT_COUNT];
+  unsigned long long timing[survgpu::PH_COUNT];
 };
 
 // Allocation failures map to SURV_E_NOMEM, anything else to SURV_E_CUDA.
@@ -281,6 +282,8 @@ int fit_common(int model, const surv_data* d, const surv_opts* o_in, double* bet
   if ((rc = ensure(ws, W::DK, 4 * (size_t)K, &dk))) return rc;
   if ((rc = ensure(ws, W::CK, 4 * (size_t)K, &ck))) return rc;
   if ((rc = ensure(ws, W::GK, 8 * (size_t)K, &Gk))) return rc;
+  void* Gkff = nullptr;
+  if ((rc = ensure(ws, W::GKFF, 8 * (size_t)K, &Gkff))) return rc;
   if ((rc = ensure(ws, W::REC, accsz * (size_t)K * M, &rec))) return rc;
   if ((rc = ensure(ws, W::E, tsz * (size_t)n, &e))) return rc;
   if ((rc = ensure(ws, W::ETA, 8 * (size_t)n, &eta))) return rc;
@@ -299,7 +302,8 @@ int fit_common(int model, const surv_data* d, const surv_opts* o_in, double* bet
                                      static_cast<int32_t*>(ck), &ctrl->total_events, s));
   launches += 2;
   if (model == SURV_FG) {
-    CUDA_TRY(survgpu::prep_km(static_cast<int32_t*>(gend), static_cast<int32_t*>(ck), K, static_cast<double*>(Gk), s));
+    CUDA_TRY(survgpu::prep_km(static_cast<int32_t*>(gend), static_cast<int32_t*>(ck), K, static_cast<double*>(Gk),
+                              static_cast<float2*>(Gkff), s));
     CUDA_TRY(survgpu::prep_w2(static_cast<int32_t*>(gend), K, status_p, static_cast<double*>(Gk), w2, prec, s));
     launches += 2;
   }
@@ -362,6 +366,7 @@ int fit_common(int model, const surv_data* d, const surv_opts* o_in, double* bet
   P.gend = static_cast<const int32_t*>(gend);
   P.dk = static_cast<const int32_t*>(dk);
   P.Gk = static_cast<const double*>(Gk);
+  P.Gkff = static_cast<const float2*>(Gkff);
   P.wk0 = static_cast<const int32_t*>(wk0);
   P.col_ptr = static_cast<const int64_t*>(colptr_d);
   P.row_idx = static_cast<const int32_t*>(rowidx_d);
@@ -381,6 +386,7 @@ int fit_common(int model, const surv_data* d, const surv_opts* o_in, double* bet
   P.counters = ctrl->counters;
   P.err = &ctrl->err;
   P.out = ctrl->out;
+  P.timing = ctrl->timing;
   P.penalty = single_j >= 0 ? 0 : o.penalty;
   P.max_sweeps = o.max_sweeps;
   P.tol = o.tol;
@@ -428,6 +434,7 @@ int fit_common(int model, const surv_data* d, const surv_opts* o_in, double* bet
     info->eta_updates = (int64_t)hc.out[survgpu::OUT_ETA_UPDATES];
     info->kernel_launches = launches;
     info->ccd_kernel_ms = kernel_ms;
+    for (int i = 0; i < 6; ++i) info->phase_ms[i] = (double)hc.timing[i] * 1e-6;
   }
   if (hc.err != 0) {
     set_error("device-side wait expired (error word 0x%x)", hc.err);
@@ -548,7 +555,7 @@ int surv_groups(const int32_t* time, const int8_t* status, int64_t n, int64_t ma
   CUDA_TRY(survgpu::prep_write_ends(tp, n, static_cast<const int32_t*>(blockcnt), static_cast<int32_t*>(gend), s));
   CUDA_TRY(survgpu::prep_group_stats(static_cast<int32_t*>(gend), K, sp, static_cast<int32_t*>(dk),
                                      static_cast<int32_t*>(ck), &ctrl->total_events, s));
-  CUDA_TRY(survgpu::prep_km(static_cast<int32_t*>(gend), static_cast<int32_t*>(ck), K, static_cast<double*>(Gk), s));
+  CUDA_TRY(survgpu::prep_km(static_cast<int32_t*>(gend), static_cast<int32_t*>(ck), K, static_cast<double*>(Gk), nullptr, s));
   if (gend_out) CUDA_TRY(cudaMemcpyAsync(gend_out, gend, 4 * (size_t)K, cudaMemcpyDefault, s));
   if (dk_out) CUDA_TRY(cudaMemcpyAsync(dk_out, dk, 4 * (size_t)K, cudaMemcpyDefault, s));
   if (Gk_out) CUDA_TRY(cudaMemcpyAsync(Gk_out, Gk, 8 * (size_t)K, cudaMemcpyDefault, s));

@@ -97,14 +97,20 @@ __device__ __forceinline__ double acc_div(double a, double b) { return a / b; }
 __device__ __forceinline__ ff acc_mul(ff a, ff b) { return ff_mul(a, b); }
 __device__ __forceinline__ double acc_mul(double a, double b) { return a * b; }
 __device__ __forceinline__ ff acc_scale(ff a, int d) { return ff_mul_f(a, (float)d); }
+// a base value held both as double and as float-float: pick the accumulator's form
+template <typename A> __device__ __forceinline__ A acc_base(double d, ff f);
+template <> __device__ __forceinline__ ff acc_base<ff>(double, ff f) { return f; }
+template <> __device__ __forceinline__ double acc_base<double>(double d, ff) { return d; }
+__device__ __forceinline__ ff acc_recip(ff a) { return ff_div({1.f, 0.f}, a); }
+__device__ __forceinline__ double acc_recip(double a) { return 1.0 / a; }
 __device__ __forceinline__ double acc_scale(double a, int d) { return a * (double)d; }
 
 // Grid exchange: every CTA writes its payload slot, then thread 0 fences and
-// adds 1 to the exchange counter; waiters poll the counter with relaxed loads
-// until it reaches `target` (= exchanges so far x G) and fence once before
-// reading the payloads through L2.  A counter costs one L2 atomic per CTA and
-// one polled word, which measured faster on GB300 than polling one flag per
-// CTA.  The wait is bounded by limit_ns.
+// adds 1 to the exchange counter; lane 0 of the waiting warp polls the counter
+// with acquire loads until it reaches `target` (= exchanges so far x G), then
+// the warp reads the payloads through L2.  One counter measured faster on
+// GB300 than one flag per CTA or counters spread over several lines.  The
+// wait is bounded by limit_ns.
 __device__ __forceinline__ void exchange_arrive(unsigned* counter) {
   __threadfence();
   atomicAdd(counter, 1u);
@@ -118,8 +124,8 @@ __device__ __forceinline__ bool exchange_wait(const unsigned* counter, unsigned 
   for (;;) {
     unsigned v = 0, bad = 0;
     if (lane == 0) {
-      asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(counter) : "memory");
-      bad = ld_volatile(err);
+      v = ld_acquire(counter);
+      if (v < target) bad = ld_volatile(err);
     }
     v = __shfl_sync(0xffffffffu, v, 0);
     bad = __shfl_sync(0xffffffffu, bad, 0);
@@ -131,7 +137,7 @@ __device__ __forceinline__ bool exchange_wait(const unsigned* counter, unsigned 
       return false;
     }
   }
-  asm volatile("fence.acq_rel.gpu;" ::: "memory");
+  __syncwarp();
   return true;
 }
 
@@ -195,14 +201,16 @@ __global__ void __launch_bounds__(Cfg<MODEL, LAYOUT, T>::MAXT, 1) ccd_kernel(con
   constexpr int TILE = C::TILE;
   constexpr int ND = C::ND;
   constexpr int NS = C::NS;
+  constexpr int SR = 4;  // rounds of 32 nonzeros whose loads are issued before the dense tiles
 
-  __shared__ A s_wtot[kMaxWarpsPerCta][M];
-  __shared__ A s_woff[kMaxWarpsPerCta][M];
-  __shared__ A s_T[M];
-  __shared__ A s_tot[M];
-  __shared__ A s_red[kMaxWarpsPerCta][2];
-  __shared__ double s_redl[kMaxWarpsPerCta];
-  __shared__ double s_scal[8];
+  __shared__ double s_wtot[kMaxWarpsPerCta][M];  // warp totals of the pass
+  __shared__ double s_base[kMaxWarpsPerCta][M];  // prefix before each warp: CTAs before + warps before
+  __shared__ ff s_baseff[kMaxWarpsPerCta][M];    // the same as float-float
+  __shared__ double s_tot[M];                    // grand totals (Fine-Gray suffix)
+  __shared__ ff s_totff[M];
+  __shared__ double s_red[kMaxWarpsPerCta][3];
+  __shared__ double s_bc[8];                     // scalars broadcast by thread 0
+  __shared__ float s_delta[2];                   // applied step as float-float
   __shared__ int s_flag[2];
 
   const int tid = threadIdx.x;
@@ -223,40 +231,73 @@ __global__ void __launch_bounds__(Cfg<MODEL, LAYOUT, T>::MAXT, 1) ccd_kernel(con
   const int64_t cta_row_hi = min(min((int64_t)(c + 1) * WPC * P.wpw, nwords) * 32, n);
   const int k_lo = P.wk0[gw], k_hi = P.wk0[gw + 1];
   const int kc_lo = P.wk0[c * WPC], kc_hi = P.wk0[(c + 1) * WPC];
+  const int nends = kc_hi - kc_lo;
 
   const T* e = reinterpret_cast<const T*>(P.e);
   const T* w2 = reinterpret_cast<const T*>(P.w2);
   A* rec = reinterpret_cast<A*>(P.rec);
   const int nw1 = P.nwarps + 1;
-
-  unsigned epoch = P.epoch0;
-  int sweep = 0;
-  double f_prev = 0.0, f_prev2 = 0.0, ll_last = 0.0;
-  int converged = 0;
-  long long eta_updates = 0, passes = 0;
   const bool single = P.single_j >= 0;
 
-  for (;;) {
-    bool finished = false;
-    for (int jj = 0; jj < P.p && !finished; ++jj) {
+  // control state, meaningful in thread 0 only (identical in every CTA)
+  int sweep = 0, converged = 0;
+  double f_prev = 0.0, f_prev2 = 0.0, ll_last = 0.0;
+  long long eta_updates = 0;
+  unsigned passes = 0;
+  bool finished = false;
+  // phase timers (thread 0): CTA 0 reports its phases, every CTA its pass time
+  unsigned long long ph[5] = {0, 0, 0, 0, 0};
+  uint64_t tmark = 0;
+  auto lap = [&](int i) {
+    if (tid == 0) {
+      const uint64_t t = global_ns();
+      ph[i] += t - tmark;
+      tmark = t;
+    }
+  };
+
+  while (!finished) {
+    for (int jj = 0; jj < P.p; ++jj) {
       const int j = single ? P.single_j : jj;
       const bool eval = single || jj == 0;
-      ++epoch;
       ++passes;
-      const int par = epoch & 1;
-      if (ld_volatile(P.err) != 0u) { finished = true; break; }
+      const int par = passes & 1;
       // beta_j and Delta_j are read before this CTA publishes anything for
-      // this coordinate: CTA 0 rewrites them only after exchange #2, which
+      // this coordinate; CTA 0 rewrites them only after exchange #2, which
       // needs every CTA's partial.  L2 loads: the writer is another SM.
-      const double bj = __ldcg(P.beta + j);
-      const double wj = __ldcg(P.width + j);
+      if (tid == 0) {
+        s_bc[5] = __ldcg(P.beta + j);
+        s_bc[6] = __ldcg(P.width + j);
+        tmark = global_ns();
+      }
 
       // ------------------------------------------------ step 2: warp pass
+      // sparse part first issues the loads of its first SR rounds so their
+      // latency overlaps the dense tiles
+      int sa = 0, sb = 0;
+      const int32_t* ri = nullptr;
+      const T* vals = nullptr;
+      int prow[SR];
+      T pval[SR];
+      if (LAYOUT == 0) {
+        const int64_t cb = P.col_ptr[j];
+        ri = P.row_idx + cb;
+        vals = P.values ? reinterpret_cast<const T*>(P.values) + cb : nullptr;
+        sa = P.woff[(size_t)j * nw1 + gw];
+        sb = P.woff[(size_t)j * nw1 + gw + 1];
+#pragma unroll
+        for (int r = 0; r < SR; ++r) {
+          const int i = sa + 32 * r + lane;
+          const bool valid = i < sb;
+          prow[r] = valid ? ri[i] : INT_MAX;
+          pval[r] = valid ? (vals ? vals[i] : T(1)) : T(0);
+        }
+      }
+
       A tot[M];
 #pragma unroll
       for (int m = 0; m < M; ++m) acc_zero(tot[m]);
       {
-        // dense part: rows [row_lo, row_hi) in tiles of TILE rows
         A acc[ND];
 #pragma unroll
         for (int d = 0; d < ND; ++d) acc_zero(acc[d]);
@@ -330,24 +371,13 @@ __global__ void __launch_bounds__(Cfg<MODEL, LAYOUT, T>::MAXT, 1) ccd_kernel(con
         for (int d = 0; d < ND; ++d) tot[C::dmap(d)] = warp_sum(acc[d]);
       }
       if (LAYOUT == 0 && NS > 0) {
-        // sparse part: nonzeros of column j inside the warp's rows
-        const int64_t cb = P.col_ptr[j];
-        const int32_t* ri = P.row_idx + cb;
-        const T* vals = P.values ? reinterpret_cast<const T*>(P.values) + cb : nullptr;
-        const int a = P.woff[(size_t)j * nw1 + gw];
-        const int b = P.woff[(size_t)j * nw1 + gw + 1];
+        // sparse part: the nonzeros of column j inside the warp's rows
         A sacc[NS > 0 ? NS : 1];
 #pragma unroll
         for (int s = 0; s < NS; ++s) acc_zero(sacc[s]);
         int kn = k_lo;
         int64_t next_end = kn < k_hi ? (int64_t)P.gend[kn] : LLONG_MAX;
-        for (int base = a; base < b; base += 32) {
-          const int i = base + lane;
-          const bool valid = i < b;
-          const int row = valid ? ri[i] : INT_MAX;
-          const T x = valid ? (vals ? vals[i] : T(1)) : T(0);
-          const T ev = valid ? e[row] : T(0);
-          const T wv = (MODEL == 1 && valid) ? w2[row] : T(0);
+        auto round = [&](int row, T x, T ev, T wv, int nvalid) {
           T sv[NS > 0 ? NS : 1];
           sv[0] = ev * x;
           if (NS > 1) sv[NS > 1 ? 1 : 0] = sv[0] * x;
@@ -355,8 +385,8 @@ __global__ void __launch_bounds__(Cfg<MODEL, LAYOUT, T>::MAXT, 1) ccd_kernel(con
             sv[NS > 2 ? 2 : 0] = wv * sv[0];
             sv[NS > 3 ? 3 : 0] = wv * sv[NS > 1 ? 1 : 0];
           }
-          const int nvalid = min(32, b - base);
           const int last_row = __shfl_sync(0xffffffffu, row, nvalid - 1);
+          // ends before the round's last nonzero see only part of the round
           while (next_end < (int64_t)last_row) {
 #pragma unroll
             for (int s = 0; s < NS; ++s) {
@@ -368,6 +398,24 @@ __global__ void __launch_bounds__(Cfg<MODEL, LAYOUT, T>::MAXT, 1) ccd_kernel(con
           }
 #pragma unroll
           for (int s = 0; s < NS; ++s) sacc[s] = acc_add_v(sacc[s], sv[s]);
+        };
+        T pe[SR], pw[SR];
+#pragma unroll
+        for (int r = 0; r < SR; ++r) {
+          pe[r] = prow[r] != INT_MAX ? e[prow[r]] : T(0);
+          pw[r] = (MODEL == 1 && prow[r] != INT_MAX) ? w2[prow[r]] : T(0);
+        }
+#pragma unroll
+        for (int r = 0; r < SR; ++r)
+          if (sa + 32 * r < sb) round(prow[r], pval[r], pe[r], pw[r], min(32, sb - sa - 32 * r));
+        for (int base = sa + 32 * SR; base < sb; base += 32) {
+          const int i = base + lane;
+          const bool valid = i < sb;
+          const int row = valid ? ri[i] : INT_MAX;
+          const T x = valid ? (vals ? vals[i] : T(1)) : T(0);
+          const T ev = valid ? e[row] : T(0);
+          const T wv = (MODEL == 1 && valid) ? w2[row] : T(0);
+          round(row, x, ev, wv, min(32, sb - base));
         }
 #pragma unroll
         for (int s = 0; s < NS; ++s) tot[C::smap(s)] = warp_sum(sacc[s]);
@@ -379,55 +427,58 @@ __global__ void __launch_bounds__(Cfg<MODEL, LAYOUT, T>::MAXT, 1) ccd_kernel(con
       }
       if (lane == 0)
 #pragma unroll
-        for (int m = 0; m < M; ++m) s_wtot[w][m] = tot[m];
+        for (int m = 0; m < M; ++m) s_wtot[w][m] = acc_to_d(tot[m]);
       __syncthreads();
+      lap(PH_PASS);
 
       // ------------------------------ CTA combine and grid exchange #1
       if (w == 0) {
+        double agg[M];
 #pragma unroll
-        for (int m = 0; m < M; ++m) {
-          A v;
-          acc_zero(v);
-          if (lane < WPC) v = s_wtot[lane][m];
-          A incl = warp_inclusive_scan(v, lane);
-          A excl = shfl_up(incl, 1);
-          if (lane == 0) acc_zero(excl);
-          if (lane < WPC) s_woff[lane][m] = excl;
-          A agg = shfl_idx(incl, WPC - 1);
-          if (lane == 0) {
-            unsigned* slot = P.slot_agg + ((size_t)par * G + c) * kSlotWords;
-            put_acc(slot + 2 * m, agg);
-          }
+        for (int m = 0; m < M; ++m) agg[m] = warp_sum(lane < WPC ? s_wtot[lane][m] : 0.0);
+        unsigned* slot = P.slot_agg + ((size_t)par * G + c) * kSlotWords;
+        if (lane == 0) {
+#pragma unroll
+          for (int m = 0; m < M; ++m) put_acc(slot + 2 * m, agg[m]);
+          if (c != P.withhold_cta) exchange_arrive(P.counters + 0);
         }
-        if (lane == 0 && c != P.withhold_cta) exchange_arrive(P.counters + 0);
-        bool ok = exchange_wait(P.counters + 0, (unsigned)passes * (unsigned)G, P.err, P.timeout_ns);
+        bool ok = exchange_wait(P.counters + 0, passes * (unsigned)G, P.err, P.timeout_ns);
         if (lane == 0) s_flag[0] = ok ? 0 : 1;
         if (ok) {
-          // exclusive prefix over CTAs < c, and (Fine-Gray) the grand total
-          A pre[M], all[M];
+          // exclusive prefix over CTAs < c (fixed order), grand totals (FG),
+          // then the base of every warp of this CTA
+          double pre[M], all[M];
 #pragma unroll
-          for (int m = 0; m < M; ++m) { acc_zero(pre[m]); acc_zero(all[m]); }
+          for (int m = 0; m < M; ++m) { pre[m] = 0.0; all[m] = 0.0; }
           for (int q = lane; q < G; q += 32) {
-            const unsigned* slot = P.slot_agg + ((size_t)par * G + q) * kSlotWords;
+            const unsigned* sq = P.slot_agg + ((size_t)par * G + q) * kSlotWords;
 #pragma unroll
             for (int m = 0; m < M; ++m) {
-              A v = get_acc<A>(slot + 2 * m);
-              if (q < c) pre[m] = acc_add(pre[m], v);
-              if (MODEL == 1) all[m] = acc_add(all[m], v);
+              const double v = get_acc<double>(sq + 2 * m);
+              if (q < c) pre[m] += v;
+              if (MODEL == 1) all[m] += v;
             }
           }
 #pragma unroll
           for (int m = 0; m < M; ++m) {
-            A t = warp_sum(pre[m]);
-            if (lane == 0) s_T[m] = t;
+            const double T_c = warp_sum(pre[m]);
             if (MODEL == 1) {
-              A a2 = warp_sum(all[m]);
-              if (lane == 0) s_tot[m] = a2;
+              const double a2 = warp_sum(all[m]);
+              if (lane == 0) { s_tot[m] = a2; s_totff[m] = d_to_ff(a2); }
+            }
+            // exclusive scan of the warp totals of this CTA
+            double v = lane < WPC ? s_wtot[lane][m] : 0.0;
+            double incl = warp_inclusive_scan(v, lane);
+            double excl = shfl_up(incl, 1);
+            if (lane == 0) excl = 0.0;
+            if (lane < WPC) {
+              const double b = T_c + excl;
+              s_base[lane][m] = b;
+              s_baseff[lane][m] = d_to_ff(b);
             }
           }
           // penalty and delta^T eta = sum_q beta_q (delta^T X_q) for the
-          // objective.  Read here, before this CTA publishes its partial:
-          // CTA 0 rewrites beta_j only after exchange #2.
+          // objective, read before this CTA publishes its partial
           if (eval) {
             double pen = 0.0, lin = 0.0;
             for (int q = lane; q < P.p; q += 32) {
@@ -438,62 +489,90 @@ __global__ void __launch_bounds__(Cfg<MODEL, LAYOUT, T>::MAXT, 1) ccd_kernel(con
             }
             lin = warp_sum(lin);
             pen = warp_sum(pen);
-            if (lane == 0) { s_scal[4] = lin; s_scal[3] = pen; }
+            if (lane == 0) { s_bc[3] = pen; s_bc[4] = lin; }
           }
         }
       }
       __syncthreads();
+      lap(PH_EXCHANGE1);
       if (s_flag[0]) { finished = true; break; }
 
       // ------------------------------ steps 3-4: transform at group ends
-      A pg1, pg2;
-      acc_zero(pg1);
-      acc_zero(pg2);
-      double pl = 0.0;
-      for (int k = kc_lo + tid; k < kc_hi; k += NT) {
-        const int d = P.dk[k];
-        if (d == 0) continue;
-        const int64_t row = P.gend[k];
-        const int wl = (int)((row >> 5) / P.wpw) - c * WPC;
-        A Pm[M];
+      // Few ends per CTA: one end per thread in FP64 (latency-bound).  Many
+      // ends: float-float (FP64 throughput on GB300 is ~1/70 of FP32).
+      double pg1 = 0.0, pg2 = 0.0, pl = 0.0;
+      int nw_red;
+      if (nends <= NT) {
+        nw_red = (nends + 31) >> 5;
+        if (tid < nends) {
+          const int k = kc_lo + tid;
+          const int d = P.dk[k];
+          if (d != 0) {
+            const int wl = (int)((P.gend[k] >> 5) / P.wpw) - c * WPC;
+            double Pm[M];
 #pragma unroll
-        for (int m = 0; m < M; ++m) Pm[m] = acc_add(acc_add(s_T[m], s_woff[wl][m]), rec[(size_t)k * M + m]);
-        A den = Pm[0], num1 = Pm[1], num2 = Pm[2];
-        if (MODEL == 1) {
-          // R_2 part: G(t_k) times the suffix strictly after the group end
-          A Gk = acc_from_d(P.Gk[k], (A*)nullptr);
-          A q0 = acc_add(s_tot[3], acc_neg(Pm[3]));
-          A q1 = acc_add(s_tot[4], acc_neg(Pm[4]));
-          A q2 = acc_add(s_tot[5], acc_neg(Pm[5]));
-          den = acc_add(den, acc_mul(Gk, q0));
-          num1 = acc_add(num1, acc_mul(Gk, q1));
-          num2 = acc_add(num2, acc_mul(Gk, q2));
+            for (int m = 0; m < M; ++m) Pm[m] = s_base[wl][m] + acc_to_d(rec[(size_t)k * M + m]);
+            double den = Pm[0], num1 = Pm[1], num2 = Pm[2];
+            if (MODEL == 1) {
+              const double g = P.Gk[k];
+              den += g * (s_tot[3] - Pm[3]);
+              num1 += g * (s_tot[4] - Pm[4]);
+              num2 += g * (s_tot[5] - Pm[5]);
+            }
+            const double inv = 1.0 / den;
+            const double Gr = num1 * inv, H = num2 * inv;
+            pg1 = d * Gr;
+            pg2 = d * (H - Gr * Gr);
+            if (eval) pl = d * log(den);
+          }
         }
-        A Gr = acc_div(num1, den);
-        A H = acc_div(num2, den);
-        pg1 = acc_add(pg1, acc_scale(Gr, d));
-        pg2 = acc_add(pg2, acc_scale(acc_add(H, acc_neg(acc_mul(Gr, Gr))), d));
-        if (eval) pl += (double)d * log(acc_to_d(den));
+        if (w < nw_red) {
+          pg1 = warp_sum(pg1);
+          pg2 = warp_sum(pg2);
+          pl = warp_sum(pl);
+          if (lane == 0) { s_red[w][0] = pg1; s_red[w][1] = pg2; s_red[w][2] = pl; }
+        }
+      } else {
+        nw_red = WPC;
+        A fg1, fg2;
+        acc_zero(fg1);
+        acc_zero(fg2);
+        for (int k = kc_lo + tid; k < kc_hi; k += NT) {
+          const int d = P.dk[k];
+          if (d == 0) continue;
+          const int wl = (int)((P.gend[k] >> 5) / P.wpw) - c * WPC;
+          A Pm[M];
+#pragma unroll
+          for (int m = 0; m < M; ++m) Pm[m] = acc_add(acc_base<A>(s_base[wl][m], s_baseff[wl][m]), rec[(size_t)k * M + m]);
+          A den = Pm[0], num1 = Pm[1], num2 = Pm[2];
+          if (MODEL == 1) {
+            const float2 gf = P.Gkff[k];
+            const A g = acc_base<A>(P.Gk[k], ff{gf.x, gf.y});
+            den = acc_add(den, acc_mul(g, acc_add(acc_base<A>(s_tot[3], s_totff[3]), acc_neg(Pm[3]))));
+            num1 = acc_add(num1, acc_mul(g, acc_add(acc_base<A>(s_tot[4], s_totff[4]), acc_neg(Pm[4]))));
+            num2 = acc_add(num2, acc_mul(g, acc_add(acc_base<A>(s_tot[5], s_totff[5]), acc_neg(Pm[5]))));
+          }
+          const A inv = acc_recip(den);
+          const A Gr = acc_mul(num1, inv);
+          const A H = acc_mul(num2, inv);
+          fg1 = acc_add(fg1, acc_scale(Gr, d));
+          fg2 = acc_add(fg2, acc_scale(acc_add(H, acc_neg(acc_mul(Gr, Gr))), d));
+          if (eval) pl += (double)d * log(acc_to_d(den));
+        }
+        fg1 = warp_sum(fg1);
+        fg2 = warp_sum(fg2);
+#pragma unroll
+        for (int dl = 16; dl > 0; dl >>= 1) pl += __shfl_down_sync(0xffffffffu, pl, dl);
+        if (lane == 0) { s_red[w][0] = acc_to_d(fg1); s_red[w][1] = acc_to_d(fg2); s_red[w][2] = pl; }
       }
-      pg1 = warp_sum(pg1);
-      pg2 = warp_sum(pg2);
-#pragma unroll
-      for (int dlt = 16; dlt > 0; dlt >>= 1) pl += __shfl_down_sync(0xffffffffu, pl, dlt);
-      if (lane == 0) { s_red[w][0] = pg1; s_red[w][1] = pg2; s_redl[w] = pl; }
       __syncthreads();
+      lap(PH_TRANSFORM);
 
-      // ------------------------------ grid exchange #2: (g1, g2, l) partials
+      // ------------------------------ grid exchange #2, Newton step
       if (w == 0) {
-        A a1, a2;
-        acc_zero(a1);
-        acc_zero(a2);
-        double al = 0.0;
-        if (lane < WPC) { a1 = s_red[lane][0]; a2 = s_red[lane][1]; al = s_redl[lane]; }
-        a1 = warp_sum(a1);
-        a2 = warp_sum(a2);
-#pragma unroll
-        for (int dlt = 16; dlt > 0; dlt >>= 1) al += __shfl_down_sync(0xffffffffu, al, dlt);
-        al = __shfl_sync(0xffffffffu, al, 0);
+        const double a1 = warp_sum(lane < nw_red ? s_red[lane][0] : 0.0);
+        const double a2 = warp_sum(lane < nw_red ? s_red[lane][1] : 0.0);
+        const double al = warp_sum(lane < nw_red ? s_red[lane][2] : 0.0);
         unsigned* slot = P.slot_part + ((size_t)par * G + c) * kSlotWords;
         if (lane == 0) {
           put_acc(slot + 0, a1);
@@ -501,107 +580,115 @@ __global__ void __launch_bounds__(Cfg<MODEL, LAYOUT, T>::MAXT, 1) ccd_kernel(con
           put_acc(slot + 4, al);
           if (c != P.withhold_cta) exchange_arrive(P.counters + 1);
         }
-        bool ok = exchange_wait(P.counters + 1, (unsigned)passes * (unsigned)G, P.err, P.timeout_ns);
-        if (lane == 0) s_flag[1] = ok ? 0 : 1;
+        bool ok = exchange_wait(P.counters + 1, passes * (unsigned)G, P.err, P.timeout_ns);
+        int fin = ok ? 0 : 2;
         if (ok) {
-          A g1, g2;
-          acc_zero(g1);
-          acc_zero(g2);
-          double gl = 0.0;
+          double g1 = 0.0, g2 = 0.0, gl = 0.0;
           for (int q = lane; q < G; q += 32) {
             const unsigned* sq = P.slot_part + ((size_t)par * G + q) * kSlotWords;
-            g1 = acc_add(g1, get_acc<A>(sq + 0));
-            g2 = acc_add(g2, get_acc<A>(sq + 2));
+            g1 += get_acc<double>(sq + 0);
+            g2 += get_acc<double>(sq + 2);
             gl += get_acc<double>(sq + 4);
           }
           g1 = warp_sum(g1);
           g2 = warp_sum(g2);
           gl = warp_sum(gl);
           if (lane == 0) {
-            s_scal[0] = P.dTx[j] - acc_to_d(g1);   // l'
-            s_scal[1] = -acc_to_d(g2);             // l''
-            s_scal[2] = s_scal[4] - gl;            // l = delta^T eta - sum_k d_k log den_k
+            const double grad = P.dTx[j] - g1;   // l'
+            const double hess = -g2;             // l''
+            double applied = 0.0;
+            if (eval) {
+              const double ll = s_bc[4] - gl;    // l = delta^T eta - sum_k d_k log den_k
+              const double f = ll + s_bc[3];
+              ll_last = ll;
+              if (single) {
+                if (c == 0) {
+                  P.out[OUT_GRAD] = grad;
+                  P.out[OUT_HESS] = hess;
+                  P.out[OUT_LOGLIK] = ll;
+                  P.out[OUT_OBJECTIVE] = f;
+                }
+                fin = 1;
+              } else if (sweep >= 1 && fabs(f - f_prev) / fabs(f) < P.tol) {
+                converged = 1;
+                f_prev2 = f_prev;
+                f_prev = f;
+                fin = 1;
+              } else {
+                f_prev2 = f_prev;
+                f_prev = f;
+                if (sweep >= P.max_sweeps) fin = 1;
+              }
+            }
+            if (!fin) {
+              const double bj = s_bc[5], wj = s_bc[6];
+              const double step = newton_step(bj, grad, hess, P.penalty, P.pen[j]);
+              if (step != 0.0) applied = copysign(fmin(fabs(step), wj), step);
+              const double wnew = fmax(2.0 * fabs(applied), wj / 2.0);
+              if (c == 0) {
+                P.beta[j] = bj + applied;
+                P.width[j] = wnew;
+              }
+              if (applied != 0.0) ++eta_updates;
+            }
+            s_bc[0] = applied;
+            const ff dl = d_to_ff(applied);
+            s_delta[0] = dl.hi;
+            s_delta[1] = dl.lo;
           }
         }
+        if (lane == 0) s_flag[1] = fin;
       }
       __syncthreads();
+      lap(PH_EXCHANGE2);
       if (s_flag[1]) { finished = true; break; }
 
-      const double grad = s_scal[0], hess = s_scal[1];
-      if (eval) {
-        const double ll = s_scal[2];
-        const double f = ll + s_scal[3];
-        ll_last = ll;
-        if (single) {
-          if (c == 0 && tid == 0) {
-            P.out[OUT_GRAD] = grad;
-            P.out[OUT_HESS] = hess;
-            P.out[OUT_LOGLIK] = ll;
-            P.out[OUT_OBJECTIVE] = f;
-          }
-          finished = true;
-          break;
-        }
-        if (sweep >= 1 && fabs(f - f_prev) / fabs(f) < P.tol) {
-          converged = 1;
-          f_prev2 = f_prev;
-          f_prev = f;
-          finished = true;
-          break;
-        }
-        f_prev2 = f_prev;
-        f_prev = f;
-        if (sweep >= P.max_sweeps) { finished = true; break; }
-      }
-
-      // ------------------------------ Newton step and conditional update
-      const double step = newton_step(bj, grad, hess, P.penalty, P.pen[j]);
-      double applied = 0.0;
-      if (step != 0.0) applied = copysign(fmin(fabs(step), wj), step);
-      const double wnew = fmax(2.0 * fabs(applied), wj / 2.0);
-      if (c == 0 && tid == 0) {
-        P.beta[j] = bj + applied;
-        P.width[j] = wnew;
-      }
+      // ------------------------------ conditional update of eta and e
+      const double applied = s_bc[0];
       if (applied != 0.0) {
-        ++eta_updates;
         if (LAYOUT == 0) {
-          const int64_t cb = P.col_ptr[j];
           const int a = P.woff[(size_t)j * nw1 + c * WPC];
           const int b = P.woff[(size_t)j * nw1 + (c + 1) * WPC];
-          const int32_t* ri = P.row_idx + cb;
-          const T* vals = P.values ? reinterpret_cast<const T*>(P.values) + cb : nullptr;
-          auto* etap = reinterpret_cast<typename std::conditional<sizeof(T) == 4, float2, double>::type*>(P.eta);
-          for (int i = a + tid; i < b; i += NT) {
-            const T x = vals ? vals[i] : T(1);
-            if constexpr (sizeof(T) == 4)
-              eta_axpy(etap, reinterpret_cast<float*>(P.e), ri[i], (float)x, d_to_ff(applied));
-            else
-              eta_axpy(etap, reinterpret_cast<double*>(P.e), ri[i], (double)x, applied);
+          if constexpr (sizeof(T) == 4) {
+            const ff delta = {s_delta[0], s_delta[1]};
+            for (int i = a + tid; i < b; i += NT)
+              eta_axpy(reinterpret_cast<float2*>(P.eta), reinterpret_cast<float*>(P.e), ri[i],
+                       vals ? (float)vals[i] : 1.f, delta);
+          } else {
+            for (int i = a + tid; i < b; i += NT)
+              eta_axpy(reinterpret_cast<double*>(P.eta), reinterpret_cast<double*>(P.e), ri[i],
+                       vals ? (double)vals[i] : 1.0, applied);
           }
         } else {
           const T* xcol = reinterpret_cast<const T*>(P.X) + (size_t)j * P.ld;
-          auto* etap = reinterpret_cast<typename std::conditional<sizeof(T) == 4, float2, double>::type*>(P.eta);
-          for (int64_t i = cta_row_lo + tid; i < cta_row_hi; i += NT) {
-            if constexpr (sizeof(T) == 4)
-              eta_axpy(etap, reinterpret_cast<float*>(P.e), i, (float)xcol[i], d_to_ff(applied));
-            else
-              eta_axpy(etap, reinterpret_cast<double*>(P.e), i, (double)xcol[i], applied);
+          if constexpr (sizeof(T) == 4) {
+            const ff delta = {s_delta[0], s_delta[1]};
+            for (int64_t i = cta_row_lo + tid; i < cta_row_hi; i += NT)
+              eta_axpy(reinterpret_cast<float2*>(P.eta), reinterpret_cast<float*>(P.e), i, (float)xcol[i], delta);
+          } else {
+            for (int64_t i = cta_row_lo + tid; i < cta_row_hi; i += NT)
+              eta_axpy(reinterpret_cast<double*>(P.eta), reinterpret_cast<double*>(P.e), i, (double)xcol[i], applied);
           }
         }
       }
       __syncthreads();
+      lap(PH_UPDATE);
     }
     if (finished) break;
     ++sweep;
   }
 
+  if (tid == 0 && P.timing) {
+    atomicMax(P.timing + PH_PASS_MAX, ph[PH_PASS]);
+    if (c == 0)
+      for (int i = 0; i < 5; ++i) P.timing[i] = ph[i];
+  }
   if (c == 0 && tid == 0) {
     P.out[OUT_SWEEPS] = (double)sweep;
     P.out[OUT_CONVERGED] = (double)converged;
     P.out[OUT_ETA_UPDATES] = (double)eta_updates;
     P.out[OUT_PASSES] = (double)passes;
-    P.out[OUT_EPOCH_END] = (double)epoch;
+    P.out[OUT_EPOCH_END] = (double)passes;
     if (!single) {
       P.out[OUT_LOGLIK] = ll_last;
       P.out[OUT_OBJECTIVE] = f_prev;

@@ -33,6 +33,7 @@ struct CcdParams {
   const int32_t* gend;   // [K] group end positions
   const int32_t* dk;     // [K] events per group (Cox) / primary events (FG)
   const double* Gk;      // [K] Kaplan-Meier censoring survival at t_k (FG)
+  const float2* Gkff;    // [K] the same as float-float (hi, lo)
   const int32_t* wk0;    // [nwarps+1] first group index whose end is in warp w
 
   const int64_t* col_ptr;  // CSC
@@ -55,6 +56,7 @@ struct CcdParams {
   unsigned* counters;    // [2] arrival counters of the two exchanges (zeroed per launch)
   unsigned* err;         // device error word
   double* out;           // results, see OutIndex
+  unsigned long long* timing;  // [8] phase times (ns): see PhaseIndex
 
   int32_t penalty;
   int32_t max_sweeps;
@@ -63,6 +65,18 @@ struct CcdParams {
   int32_t withhold_cta;  // test knob: this CTA never publishes (-1 = off)
   unsigned epoch0;       // unused (counters restart at 0 every launch)
   uint64_t timeout_ns;   // bound on every grid-exchange wait
+};
+
+// Phase times accumulated by thread 0 of CTA 0 (ns), plus the largest pass
+// time over all CTAs.
+enum PhaseIndex : int {
+  PH_PASS = 0,        // warp pass (step 2) of CTA 0
+  PH_EXCHANGE1 = 1,   // CTA combine + grid exchange #1
+  PH_TRANSFORM = 2,   // group-end transform and CTA reduction (steps 3-4)
+  PH_EXCHANGE2 = 3,   // grid exchange #2 and the Newton step
+  PH_UPDATE = 4,      // eta / e update
+  PH_PASS_MAX = 5,    // largest total pass time of any CTA
+  PH_COUNT = 8,
 };
 
 enum OutIndex : int {
@@ -99,7 +113,7 @@ cudaError_t prep_count_ends(const int32_t* time, int64_t n, int32_t* blockcnt, i
 cudaError_t prep_write_ends(const int32_t* time, int64_t n, const int32_t* blockoff, int32_t* gend, cudaStream_t s);
 cudaError_t prep_group_stats(const int32_t* gend, int32_t K, const int8_t* status, int32_t* dk, int32_t* ck,
                              int32_t* total_events, cudaStream_t s);
-cudaError_t prep_km(const int32_t* gend, const int32_t* ck, int32_t K, double* Gk, cudaStream_t s);
+cudaError_t prep_km(const int32_t* gend, const int32_t* ck, int32_t K, double* Gk, float2* Gkff, cudaStream_t s);
 cudaError_t prep_w2(const int32_t* gend, int32_t K, const int8_t* status, const double* Gk, void* w2, int prec,
                     cudaStream_t s);
 cudaError_t prep_dtx_csc(const int64_t* col_ptr, const int32_t* row_idx, const void* values, int prec,

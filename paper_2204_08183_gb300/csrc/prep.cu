@@ -161,13 +161,17 @@ __global__ void k_group_stats(const int32_t* gend, int32_t K, const int8_t* stat
 
 // G(t_k) = prod_{k' >= k} (1 - c_k' / n_k'), n_k' = e_k' + 1 (Section 2.2,
 // Kaplan-Meier of the censoring times; groups k' >= k have t_k' <= t_k).
-__global__ void k_km(const int32_t* gend, const int32_t* ck, int32_t K, double* Gk) {
+__global__ void k_km(const int32_t* gend, const int32_t* ck, int32_t K, double* Gk, float2* Gkff) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
   double acc = 1.0;
   for (int64_t k = (int64_t)K - 1; k >= 0; --k) {
     const double f = 1.0 - (double)ck[k] / (double)((int64_t)gend[k] + 1);
     acc = acc * f;
     Gk[k] = acc;
+    if (Gkff) {
+      const ff v = d_to_ff(acc);
+      Gkff[k] = make_float2(v.hi, v.lo);
+    }
   }
 }
 
@@ -404,8 +408,8 @@ cudaError_t prep_group_stats(const int32_t* gend, int32_t K, const int8_t* statu
   return cudaGetLastError();
 }
 
-cudaError_t prep_km(const int32_t* gend, const int32_t* ck, int32_t K, double* Gk, cudaStream_t s) {
-  k_km<<<1, 32, 0, s>>>(gend, ck, K, Gk);
+cudaError_t prep_km(const int32_t* gend, const int32_t* ck, int32_t K, double* Gk, float2* Gkff, cudaStream_t s) {
+  k_km<<<1, 32, 0, s>>>(gend, ck, K, Gk, Gkff);
   return cudaGetLastError();
 }
 
