@@ -216,8 +216,10 @@ def run_gpu(args, rank, world):
                 "per_pass_bytes": per_pass, "passes_per_launch": passes / len(infos),
                 "eta_updates_per_launch": upd / len(infos),
                 "phase_ms_per_launch": {k: round(sum(i["phase_ms"][q] for i in infos) / len(infos), 4)
-                                        for q, k in enumerate(["pass_cta0", "exchange1", "transform",
-                                                               "exchange2_newton", "update", "pass_max_cta"])}}
+                                        for q, k in enumerate(["pass_cta0", "ex1_arrive", "ex1_wait", "ex1_after",
+                                                               "transform", "ex2_arrive", "ex2_wait",
+                                                               "ex2_newton", "update", "pass_max_cta",
+                                                               "pass_min_cta", "pass_mean_cta"])}}
 
     out = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 3), "higher_is_better": True,

@@ -135,11 +135,12 @@ typedef struct surv_fit_info {
   int64_t kernel_launches;       /* CUDA kernels launched by this call            */
   double ccd_kernel_ms;          /* device time of the CCD kernel (CUDA events on
                                     the call's stream)                            */
-  double phase_ms[6];            /* diagnostics, summed over the fit: CTA 0's
-                                    time in the row pass, exchange 1, group-end
-                                    transform, exchange 2 + Newton step, eta
-                                    update; [5] = largest row-pass total of any
-                                    CTA                                           */
+  double phase_ms[12];           /* diagnostics summed over the fit (CTA 0):
+                                    [0] row pass, [1..3] exchange 1 (arrive,
+                                    wait, after), [4] group-end transform,
+                                    [5..7] exchange 2 (arrive, wait, Newton),
+                                    [8] eta update; row-pass totals over CTAs:
+                                    [9] max, [10] min, [11] mean             */
 } surv_fit_info;
 
 /* ---- entry points ------------------------------------------------------ */

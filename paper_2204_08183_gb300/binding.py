@@ -62,7 +62,7 @@ class surv_fit_info(C.Structure):
                 ("device_error", C.c_int32), ("loglik", C.c_double), ("objective", C.c_double),
                 ("objective_prev", C.c_double), ("n_groups", C.c_int64), ("coordinate_passes", C.c_int64),
                 ("eta_updates", C.c_int64), ("kernel_launches", C.c_int64), ("ccd_kernel_ms", C.c_double),
-                ("phase_ms", C.c_double * 6)]
+                ("phase_ms", C.c_double * 12)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

@@ -348,6 +348,10 @@ int fit_common(int model, const surv_data* d, const surv_opts* o_in, double* bet
     ++launches;
   }
   CUDA_TRY(cudaMemsetAsync(slots, 0, 2 * slot_bytes, s));
+  {
+    const unsigned long long big = ~0ull;
+    CUDA_TRY(cudaMemcpyAsync(&ctrl->timing[survgpu::PH_PASS_MIN], &big, sizeof(big), cudaMemcpyHostToDevice, s));
+  }
   CUDA_TRY(cudaMemcpyAsync(&hc, ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
   if (hc.total_events <= 0) { set_error("no events"); return SURV_E_NO_EVENTS; }
@@ -434,7 +438,8 @@ int fit_common(int model, const surv_data* d, const surv_opts* o_in, double* bet
     info->eta_updates = (int64_t)hc.out[survgpu::OUT_ETA_UPDATES];
     info->kernel_launches = launches;
     info->ccd_kernel_ms = kernel_ms;
-    for (int i = 0; i < 6; ++i) info->phase_ms[i] = (double)hc.timing[i] * 1e-6;
+    for (int i = 0; i < 12; ++i) info->phase_ms[i] = (double)hc.timing[i] * 1e-6;
+    info->phase_ms[survgpu::PH_PASS_SUM] /= (double)G;  // mean over CTAs
   }
   if (hc.err != 0) {
     set_error("device-side wait expired (error word 0x%x)", hc.err);
@@ -450,6 +455,10 @@ int fit_common(int model, const surv_data* d, const surv_opts* o_in, double* bet
 }
 
 }  // namespace
+
+namespace survgpu {
+void set_last_error_text(const char* msg) { set_error("%s", msg ? msg : ""); }
+}  // namespace survgpu
 
 extern "C" {
 

@@ -71,25 +71,6 @@ __device__ __forceinline__ void eta_axpy(double* eta, double* e, int64_t i, doub
   e[i] = exp(v);
 }
 
-// Slot (de)serialisation of accumulators: 2 words each.
-__device__ __forceinline__ void put_acc(unsigned* w, ff a) {
-  w[0] = __float_as_uint(a.hi);
-  w[1] = __float_as_uint(a.lo);
-}
-__device__ __forceinline__ void put_acc(unsigned* w, double a) {
-  unsigned long long b = __double_as_longlong(a);
-  w[0] = (unsigned)(b & 0xffffffffull);
-  w[1] = (unsigned)(b >> 32);
-}
-template <typename A> __device__ __forceinline__ A get_acc(const unsigned* w);
-template <> __device__ __forceinline__ ff get_acc<ff>(const unsigned* w) {
-  return {__uint_as_float(__ldcg(w)), __uint_as_float(__ldcg(w + 1))};
-}
-template <> __device__ __forceinline__ double get_acc<double>(const unsigned* w) {
-  unsigned long long lo = __ldcg(w), hi = __ldcg(w + 1);
-  return __longlong_as_double((long long)(lo | (hi << 32)));
-}
-
 __device__ __forceinline__ ff acc_from_d(double d, ff*) { return d_to_ff(d); }
 __device__ __forceinline__ double acc_from_d(double d, double*) { return d; }
 __device__ __forceinline__ ff acc_div(ff a, ff b) { return ff_div(a, b); }
@@ -166,15 +147,18 @@ template <int MODEL, int LAYOUT, typename T>
 struct Cfg {
   static constexpr int M = MODEL == 0 ? 3 : 6;              // tuple components
   static constexpr int VEC = Vec<T>::n;                      // rows per 16-byte load
-  static constexpr int U = LAYOUT == 0 ? 8 : 4;              // loads per lane per tile
+  // loads per lane per tile: CSC streams only e, so a lane keeps 16 loads in
+  // flight; dense X and Fine-Gray stream two or three arrays
+  static constexpr int U = LAYOUT == 0 ? (MODEL == 0 ? (sizeof(T) == 4 ? 16 : 8) : 8) : 4;
   static constexpr int TILE = 32 * U * VEC;                  // rows per warp tile
   // components produced by the dense row pass
   static constexpr int ND = LAYOUT == 1 ? M : (MODEL == 0 ? 1 : 2);
   // components produced by the sparse (CSC entry) pass
   static constexpr int NS = LAYOUT == 1 ? 0 : (MODEL == 0 ? 2 : 4);
-  // threads per CTA the kernel is compiled for: 1024 (64 registers) where that
-  // does not spill, else 512 (128 registers)
-  static constexpr int MAXT = (MODEL == 0 && sizeof(T) == 4) ? 1024 : 512;
+  // threads per CTA the kernel is compiled for: 512 (128 registers).  1024
+  // threads cap a thread at 64 registers, which spills this kernel, and make
+  // every block barrier slower.
+  static constexpr int MAXT = 512;
   __device__ static constexpr int dmap(int d) { return LAYOUT == 1 ? d : (d == 0 ? 0 : 3); }
   __device__ static constexpr int smap(int s) { return s < 2 ? 1 + s : 4 + (s - 2); }
 };
@@ -246,7 +230,7 @@ __global__ void __launch_bounds__(Cfg<MODEL, LAYOUT, T>::MAXT, 1) ccd_kernel(con
   unsigned passes = 0;
   bool finished = false;
   // phase timers (thread 0): CTA 0 reports its phases, every CTA its pass time
-  unsigned long long ph[5] = {0, 0, 0, 0, 0};
+  unsigned long long ph[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   uint64_t tmark = 0;
   auto lap = [&](int i) {
     if (tid == 0) {
@@ -268,6 +252,8 @@ __global__ void __launch_bounds__(Cfg<MODEL, LAYOUT, T>::MAXT, 1) ccd_kernel(con
       if (tid == 0) {
         s_bc[5] = __ldcg(P.beta + j);
         s_bc[6] = __ldcg(P.width + j);
+        s_bc[1] = P.dTx[j];
+        s_bc[2] = P.pen[j];
         tmark = global_ns();
       }
 
@@ -432,31 +418,73 @@ __global__ void __launch_bounds__(Cfg<MODEL, LAYOUT, T>::MAXT, 1) ccd_kernel(con
       lap(PH_PASS);
 
       // ------------------------------ CTA combine and grid exchange #1
+      // Exchange payloads are laid out [parity][component][CTA] in doubles so
+      // that one warp reads every CTA's value with coalesced loads.
       if (w == 0) {
-        double agg[M];
+        double* agg_soa = reinterpret_cast<double*>(P.slot_agg) + (size_t)par * 6 * G;
+        double wv[M], excl[M];
 #pragma unroll
-        for (int m = 0; m < M; ++m) agg[m] = warp_sum(lane < WPC ? s_wtot[lane][m] : 0.0);
-        unsigned* slot = P.slot_agg + ((size_t)par * G + c) * kSlotWords;
-        if (lane == 0) {
+        for (int m = 0; m < M; ++m) wv[m] = lane < WPC ? s_wtot[lane][m] : 0.0;
 #pragma unroll
-          for (int m = 0; m < M; ++m) put_acc(slot + 2 * m, agg[m]);
-          if (c != P.withhold_cta) exchange_arrive(P.counters + 0);
+        for (int m = 0; m < M; ++m) {
+          const double a = warp_sum(wv[m]);
+          if (lane == 0) agg_soa[(size_t)m * G + c] = a;
+        }
+        if (lane == 0 && c != P.withhold_cta) exchange_arrive(P.counters + 0);
+        lap(PH_EX1_PRE);
+        // CTA-local work while the other CTAs arrive: warp offsets, and the
+        // loads of beta / dTx / penalty factors for the objective
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          const double incl = warp_inclusive_scan(wv[m], lane);
+          double ex = shfl_up(incl, 1);
+          excl[m] = lane == 0 ? 0.0 : ex;
+        }
+        double pen = 0.0, lin = 0.0;
+        if (eval) {
+          for (int q0 = 0; q0 < P.p; q0 += 32 * 4) {
+            double bq[4], dq[4], fq[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int q = q0 + 32 * u + lane;
+              bq[u] = q < P.p ? __ldcg(P.beta + q) : 0.0;
+              dq[u] = q < P.p ? P.dTx[q] : 0.0;
+              fq[u] = q < P.p ? P.pen[q] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              lin += bq[u] * dq[u];
+              if (P.penalty == 1) pen -= fq[u] * fabs(bq[u]);
+              else if (P.penalty == 2) pen -= fq[u] * bq[u] * bq[u] * 0.5;
+            }
+          }
+          lin = warp_sum(lin);
+          pen = warp_sum(pen);
         }
         bool ok = exchange_wait(P.counters + 0, passes * (unsigned)G, P.err, P.timeout_ns);
+        lap(PH_EX1_WAIT);
         if (lane == 0) s_flag[0] = ok ? 0 : 1;
         if (ok) {
-          // exclusive prefix over CTAs < c (fixed order), grand totals (FG),
-          // then the base of every warp of this CTA
+          // exclusive prefix over CTAs < c (fixed order) and grand totals
           double pre[M], all[M];
 #pragma unroll
           for (int m = 0; m < M; ++m) { pre[m] = 0.0; all[m] = 0.0; }
-          for (int q = lane; q < G; q += 32) {
-            const unsigned* sq = P.slot_agg + ((size_t)par * G + q) * kSlotWords;
+          for (int q0 = 0; q0 < G; q0 += 32 * 5) {
+            double v[M][5];
 #pragma unroll
-            for (int m = 0; m < M; ++m) {
-              const double v = get_acc<double>(sq + 2 * m);
-              if (q < c) pre[m] += v;
-              if (MODEL == 1) all[m] += v;
+            for (int u = 0; u < 5; ++u) {
+              const int q = q0 + 32 * u + lane;
+#pragma unroll
+              for (int m = 0; m < M; ++m) v[m][u] = q < G ? __ldcg(agg_soa + (size_t)m * G + q) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 5; ++u) {
+              const int q = q0 + 32 * u + lane;
+#pragma unroll
+              for (int m = 0; m < M; ++m) {
+                if (q < c) pre[m] += v[m][u];
+                if (MODEL == 1) all[m] += v[m][u];
+              }
             }
           }
 #pragma unroll
@@ -466,35 +494,17 @@ __global__ void __launch_bounds__(Cfg<MODEL, LAYOUT, T>::MAXT, 1) ccd_kernel(con
               const double a2 = warp_sum(all[m]);
               if (lane == 0) { s_tot[m] = a2; s_totff[m] = d_to_ff(a2); }
             }
-            // exclusive scan of the warp totals of this CTA
-            double v = lane < WPC ? s_wtot[lane][m] : 0.0;
-            double incl = warp_inclusive_scan(v, lane);
-            double excl = shfl_up(incl, 1);
-            if (lane == 0) excl = 0.0;
             if (lane < WPC) {
-              const double b = T_c + excl;
+              const double b = T_c + excl[m];
               s_base[lane][m] = b;
               s_baseff[lane][m] = d_to_ff(b);
             }
           }
-          // penalty and delta^T eta = sum_q beta_q (delta^T X_q) for the
-          // objective, read before this CTA publishes its partial
-          if (eval) {
-            double pen = 0.0, lin = 0.0;
-            for (int q = lane; q < P.p; q += 32) {
-              const double bq = __ldcg(P.beta + q);
-              lin += bq * P.dTx[q];
-              if (P.penalty == 1) pen -= P.pen[q] * fabs(bq);
-              else if (P.penalty == 2) pen -= P.pen[q] * bq * bq * 0.5;
-            }
-            lin = warp_sum(lin);
-            pen = warp_sum(pen);
-            if (lane == 0) { s_bc[3] = pen; s_bc[4] = lin; }
-          }
+          if (eval && lane == 0) { s_bc[3] = pen; s_bc[4] = lin; }
         }
       }
       __syncthreads();
-      lap(PH_EXCHANGE1);
+      lap(PH_EX1_POST);
       if (s_flag[0]) { finished = true; break; }
 
       // ------------------------------ steps 3-4: transform at group ends
@@ -570,31 +580,38 @@ __global__ void __launch_bounds__(Cfg<MODEL, LAYOUT, T>::MAXT, 1) ccd_kernel(con
 
       // ------------------------------ grid exchange #2, Newton step
       if (w == 0) {
+        double* part_soa = reinterpret_cast<double*>(P.slot_part) + (size_t)par * 3 * G;
         const double a1 = warp_sum(lane < nw_red ? s_red[lane][0] : 0.0);
         const double a2 = warp_sum(lane < nw_red ? s_red[lane][1] : 0.0);
         const double al = warp_sum(lane < nw_red ? s_red[lane][2] : 0.0);
-        unsigned* slot = P.slot_part + ((size_t)par * G + c) * kSlotWords;
         if (lane == 0) {
-          put_acc(slot + 0, a1);
-          put_acc(slot + 2, a2);
-          put_acc(slot + 4, al);
+          part_soa[c] = a1;
+          part_soa[G + c] = a2;
+          part_soa[2 * G + c] = al;
           if (c != P.withhold_cta) exchange_arrive(P.counters + 1);
         }
+        lap(PH_EX2_PRE);
         bool ok = exchange_wait(P.counters + 1, passes * (unsigned)G, P.err, P.timeout_ns);
+        lap(PH_EX2_WAIT);
         int fin = ok ? 0 : 2;
         if (ok) {
           double g1 = 0.0, g2 = 0.0, gl = 0.0;
-          for (int q = lane; q < G; q += 32) {
-            const unsigned* sq = P.slot_part + ((size_t)par * G + q) * kSlotWords;
-            g1 += get_acc<double>(sq + 0);
-            g2 += get_acc<double>(sq + 2);
-            gl += get_acc<double>(sq + 4);
+          for (int q0 = 0; q0 < G; q0 += 32 * 5) {
+            double v[3][5];
+#pragma unroll
+            for (int u = 0; u < 5; ++u) {
+              const int q = q0 + 32 * u + lane;
+#pragma unroll
+              for (int m = 0; m < 3; ++m) v[m][u] = q < G ? __ldcg(part_soa + (size_t)m * G + q) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 5; ++u) { g1 += v[0][u]; g2 += v[1][u]; gl += v[2][u]; }
           }
           g1 = warp_sum(g1);
           g2 = warp_sum(g2);
           gl = warp_sum(gl);
           if (lane == 0) {
-            const double grad = P.dTx[j] - g1;   // l'
+            const double grad = s_bc[1] - g1;    // l' = delta^T X_j - sum_k d_k G_k
             const double hess = -g2;             // l''
             double applied = 0.0;
             if (eval) {
@@ -622,7 +639,7 @@ __global__ void __launch_bounds__(Cfg<MODEL, LAYOUT, T>::MAXT, 1) ccd_kernel(con
             }
             if (!fin) {
               const double bj = s_bc[5], wj = s_bc[6];
-              const double step = newton_step(bj, grad, hess, P.penalty, P.pen[j]);
+              const double step = newton_step(bj, grad, hess, P.penalty, s_bc[2]);
               if (step != 0.0) applied = copysign(fmin(fabs(step), wj), step);
               const double wnew = fmax(2.0 * fabs(applied), wj / 2.0);
               if (c == 0) {
@@ -640,7 +657,7 @@ __global__ void __launch_bounds__(Cfg<MODEL, LAYOUT, T>::MAXT, 1) ccd_kernel(con
         if (lane == 0) s_flag[1] = fin;
       }
       __syncthreads();
-      lap(PH_EXCHANGE2);
+      lap(PH_EX2_POST);
       if (s_flag[1]) { finished = true; break; }
 
       // ------------------------------ conditional update of eta and e
@@ -650,10 +667,31 @@ __global__ void __launch_bounds__(Cfg<MODEL, LAYOUT, T>::MAXT, 1) ccd_kernel(con
           const int a = P.woff[(size_t)j * nw1 + c * WPC];
           const int b = P.woff[(size_t)j * nw1 + (c + 1) * WPC];
           if constexpr (sizeof(T) == 4) {
+            // loads batched 8 deep: the row indices, then eta, then the stores
             const ff delta = {s_delta[0], s_delta[1]};
-            for (int i = a + tid; i < b; i += NT)
-              eta_axpy(reinterpret_cast<float2*>(P.eta), reinterpret_cast<float*>(P.e), ri[i],
-                       vals ? (float)vals[i] : 1.f, delta);
+            float2* etap = reinterpret_cast<float2*>(P.eta);
+            float* ep = reinterpret_cast<float*>(P.e);
+            for (int i0 = a; i0 < b; i0 += 8 * NT) {
+              int rr[8];
+              float xx[8];
+              float2 qq[8];
+#pragma unroll
+              for (int u = 0; u < 8; ++u) {
+                const int i = i0 + u * NT + tid;
+                rr[u] = i < b ? ri[i] : -1;
+                xx[u] = i < b ? (vals ? (float)vals[i] : 1.f) : 0.f;
+              }
+#pragma unroll
+              for (int u = 0; u < 8; ++u) qq[u] = rr[u] >= 0 ? etap[rr[u]] : make_float2(0.f, 0.f);
+#pragma unroll
+              for (int u = 0; u < 8; ++u) {
+                if (rr[u] < 0) continue;
+                const ff v = ff_add({qq[u].x, qq[u].y}, ff_mul_f(delta, xx[u]));
+                etap[rr[u]] = make_float2(v.hi, v.lo);
+                const float ev = expf(v.hi);
+                ep[rr[u]] = fmaf(ev, v.lo, ev);
+              }
+            }
           } else {
             for (int i = a + tid; i < b; i += NT)
               eta_axpy(reinterpret_cast<double*>(P.eta), reinterpret_cast<double*>(P.e), ri[i],
@@ -680,8 +718,10 @@ __global__ void __launch_bounds__(Cfg<MODEL, LAYOUT, T>::MAXT, 1) ccd_kernel(con
 
   if (tid == 0 && P.timing) {
     atomicMax(P.timing + PH_PASS_MAX, ph[PH_PASS]);
+    atomicMin(P.timing + PH_PASS_MIN, ph[PH_PASS]);
+    atomicAdd(P.timing + PH_PASS_SUM, ph[PH_PASS]);
     if (c == 0)
-      for (int i = 0; i < 5; ++i) P.timing[i] = ph[i];
+      for (int i = 0; i < 9; ++i) P.timing[i] = ph[i];
   }
   if (c == 0 && tid == 0) {
     P.out[OUT_SWEEPS] = (double)sweep;

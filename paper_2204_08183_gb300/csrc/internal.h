@@ -67,16 +67,22 @@ struct CcdParams {
   uint64_t timeout_ns;   // bound on every grid-exchange wait
 };
 
-// Phase times accumulated by thread 0 of CTA 0 (ns), plus the largest pass
-// time over all CTAs.
+// Phase times accumulated by thread 0 of CTA 0 (ns), plus statistics of the
+// per-CTA total pass time.
 enum PhaseIndex : int {
   PH_PASS = 0,        // warp pass (step 2) of CTA 0
-  PH_EXCHANGE1 = 1,   // CTA combine + grid exchange #1
-  PH_TRANSFORM = 2,   // group-end transform and CTA reduction (steps 3-4)
-  PH_EXCHANGE2 = 3,   // grid exchange #2 and the Newton step
-  PH_UPDATE = 4,      // eta / e update
-  PH_PASS_MAX = 5,    // largest total pass time of any CTA
-  PH_COUNT = 8,
+  PH_EX1_PRE = 1,     // CTA combine, payload, arrival at exchange #1
+  PH_EX1_WAIT = 2,    // waiting for the other CTAs (exchange #1)
+  PH_EX1_POST = 3,    // prefix / totals after exchange #1
+  PH_TRANSFORM = 4,   // group-end transform and CTA reduction (steps 3-4)
+  PH_EX2_PRE = 5,     // payload and arrival at exchange #2
+  PH_EX2_WAIT = 6,    // waiting for the other CTAs (exchange #2)
+  PH_EX2_POST = 7,    // final sums and the Newton step
+  PH_UPDATE = 8,      // eta / e update
+  PH_PASS_MAX = 9,    // largest total pass time of any CTA
+  PH_PASS_MIN = 10,   // smallest total pass time of any CTA
+  PH_PASS_SUM = 11,   // sum over CTAs of the total pass time
+  PH_COUNT = 16,
 };
 
 enum OutIndex : int {
@@ -136,6 +142,9 @@ cudaError_t prep_fill_f64(double* v, double value, int64_t count, cudaStream_t s
 cudaError_t prep_convert_dense(const void* src, int src_dtype, int64_t n, int64_t p, void* dst, int prec,
                                int64_t ld, cudaStream_t s);
 cudaError_t prep_convert_vec(const void* src, int src_dtype, int64_t count, void* dst, int prec, cudaStream_t s);
+
+// Text returned by surv_last_error() on the calling thread (api.cu).
+void set_last_error_text(const char* msg);
 
 // ---- sort (sort.cu) -----------------------------------------------------
 // Workspace bytes needed by radix_sort_desc for n elements.
