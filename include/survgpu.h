@@ -196,6 +196,36 @@ int loglik_grad_hess(const surv_data *data, int32_t model, const double *beta,
 int surv_groups(const int32_t *time, const int8_t *status, int64_t n, int64_t max_groups, int64_t *K,
                 int32_t *gend, int32_t *dk, double *Gk, void *stream);
 
+/* Allocation-free variant of loglik_grad_hess.  The paper has no counterpart;
+ * this entry point is for callers that cannot allocate device memory while
+ * they run, for example a host program whose device memory is entirely owned
+ * by another allocator (a framework's caching pool, or a fixed budget taken
+ * at start-up), or a latency-sensitive loop that cannot afford cudaMalloc and
+ * cudaFree, which may synchronise the whole device.  It returns the same
+ * (l, l', l'') as loglik_grad_hess for coordinate j and calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ *
+ * Scratch: one fixed 16 MiB array in device memory, reserved by every GPU
+ * that loads this library until the process exits.  A problem needs about
+ * 12 bytes per subject (Cox, FP32; 16-24 for Fine-Gray or FP64), 52-76 bytes
+ * per tie group and, for CSC, 19.5 KB per covariate; for example one million
+ * subjects with 3650 distinct times and p = 100 fit.  A larger problem is
+ * rejected with SURV_E_INVALID before any work is queued.  p <= 4096.
+ * The first call on a device looks up the array's device address and caches
+ * it; make that first call before any stream capture.  All calls on a device
+ * share the array, which keeps the last call's contents (the call zeroes
+ * what must start at zero itself); calls that overlap on the GPU, from other
+ * host threads or streams, race on it and must be serialised by the caller.
+ *   data: time, status and X must be device arrays (there is no staging
+ *   buffer); X values in the dtype that `precision` uses (SURV_PREC_F32C:
+ *   float32, SURV_PREC_F64: float64; CSC values may be NULL); dense X with a
+ *   16-byte aligned base and n divisible by 4.  beta [p] host or device.
+ *   loglik, grad, hess: host doubles (any may be NULL).  stream:
+ *   cudaStream_t or NULL.  Errors as loglik_grad_hess, plus SURV_E_INVALID
+ *   for the limits above. */
+int loglik_grad_hess_noalloc(const surv_data *data, int32_t model, const double *beta, int32_t j,
+                             double *loglik, double *grad, double *hess, int32_t precision, void *stream);
+
 /* Short name of a return code (static string). */
 const char *surv_strerror(int code);
 

@@ -40,8 +40,8 @@ SURV_FLAG_TEST_STALL = 1
 
 # exported symbols, in the order the header declares them
 EXPORTS = ["surv_opts_default", "surv_workspace_create", "surv_workspace_destroy", "surv_sort_desc",
-           "cox_fit", "fg_fit", "loglik_grad_hess", "surv_groups", "surv_strerror", "surv_last_error",
-           "surv_version"]
+           "cox_fit", "fg_fit", "loglik_grad_hess", "surv_groups", "loglik_grad_hess_noalloc",
+           "surv_strerror", "surv_last_error", "surv_version"]
 
 
 class surv_data(C.Structure):
@@ -94,6 +94,9 @@ def load(path: str = LIB_PATH):
                                      C.POINTER(surv_opts)]
     lib.surv_groups.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.POINTER(C.c_int64), C.c_void_p,
                                 C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.loglik_grad_hess_noalloc.argtypes = [C.POINTER(surv_data), C.c_int32, C.c_void_p, C.c_int32,
+                                             C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                             C.POINTER(C.c_double), C.c_int32, C.c_void_p]
     lib.surv_strerror.argtypes = [C.c_int]
     lib.surv_strerror.restype = C.c_char_p
     lib.surv_last_error.restype = C.c_char_p
@@ -259,6 +262,18 @@ def loglik_grad_hess(data: SurvData, model: str, beta, j: int, **kw):
     m = {"cox": SURV_COX, "fg": SURV_FG}[model]
     rc = load().loglik_grad_hess(C.byref(data.c), m, C.c_void_p(_ptr(beta)), int(j), C.byref(l), C.byref(g),
                                  C.byref(h), C.byref(opts))
+    _check(rc)
+    return l.value, g.value, h.value
+
+
+def loglik_grad_hess_noalloc(data: SurvData, model: str, beta, j: int, precision="f32c", stream=None):
+    """Same as loglik_grad_hess through the allocation-free entry point: the
+    library uses its fixed device scratch array and allocates nothing (the
+    cohort must already be on the GPU)."""
+    l, g, h = C.c_double(), C.c_double(), C.c_double()
+    m = {"cox": SURV_COX, "fg": SURV_FG}[model]
+    rc = load().loglik_grad_hess_noalloc(C.byref(data.c), m, C.c_void_p(_ptr(beta)), int(j), C.byref(l),
+                                         C.byref(g), C.byref(h), SURV_PREC[precision], _stream(stream))
     _check(rc)
     return l.value, g.value, h.value
 
