@@ -116,6 +116,13 @@ typedef struct surv_opts {
  * so every other CTA's bounded wait expires; the call must then return
  * SURV_E_DEVICE_TIMEOUT and leave the device usable. */
 #define SURV_FLAG_TEST_STALL 1
+/* Run a fit as one persistent cooperative launch (grid-wide exchanges in
+ * device memory, bounded waits) instead of the default schedule of two
+ * kernels per coordinate replayed as a CUDA graph, one replay per sweep.
+ * Both schedules compute the same quantities in the same order of
+ * coordinates; this flag exists to compare them.  loglik_grad_hess always
+ * uses the persistent kernel. */
+#define SURV_FLAG_PERSISTENT 2
 
 /* Fill *opts with defaults: no penalty, FP32-compensated precision,
  * tol 1e-8, max_sweeps 1000, default stream, no workspace. */
@@ -135,12 +142,15 @@ typedef struct surv_fit_info {
   int64_t kernel_launches;       /* CUDA kernels launched by this call            */
   double ccd_kernel_ms;          /* device time of the CCD kernel (CUDA events on
                                     the call's stream)                            */
-  double phase_ms[12];           /* diagnostics summed over the fit (CTA 0):
+  double phase_ms[16];           /* diagnostics summed over the fit (CTA 0):
                                     [0] row pass, [1..3] exchange 1 (arrive,
                                     wait, after), [4] group-end transform,
                                     [5..7] exchange 2 (arrive, wait, Newton),
                                     [8] eta update; row-pass totals over CTAs:
-                                    [9] max, [10] min, [11] mean             */
+                                    [9] max, [10] min, [11] mean; largest
+                                    dense [12] and sparse [13] part of the
+                                    pass; CTA 0 exchange-1 warp sums [14] and
+                                    payload stores [15] (inside [1])        */
 } surv_fit_info;
 
 /* ---- entry points ------------------------------------------------------ */

@@ -37,6 +37,7 @@ SURV_COX, SURV_FG = 0, 1
 SURV_PEN = {"none": 0, "l1": 1, "l2": 2}
 SURV_PREC = {"f32c": 0, "f64": 1}
 SURV_FLAG_TEST_STALL = 1
+SURV_FLAG_PERSISTENT = 2
 
 # exported symbols, in the order the header declares them
 EXPORTS = ["surv_opts_default", "surv_workspace_create", "surv_workspace_destroy", "surv_sort_desc",
@@ -62,7 +63,7 @@ class surv_fit_info(C.Structure):
                 ("device_error", C.c_int32), ("loglik", C.c_double), ("objective", C.c_double),
                 ("objective_prev", C.c_double), ("n_groups", C.c_int64), ("coordinate_passes", C.c_int64),
                 ("eta_updates", C.c_int64), ("kernel_launches", C.c_int64), ("ccd_kernel_ms", C.c_double),
-                ("phase_ms", C.c_double * 12)]
+                ("phase_ms", C.c_double * 16)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

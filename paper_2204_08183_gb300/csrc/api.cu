@@ -2,6 +2,7 @@
 // staging of host buffers, workspace management and the launch sequence
 // prep kernels -> persistent CCD kernel.  No arithmetic of the method runs
 // on the host; the host reads back only sizes, error words and results.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -19,10 +20,11 @@ struct surv_workspace {
   };
   enum Id {
     TIME, STATUS, COLPTR, ROWIDX, VALUES, XD, E, ETA, W2, GEND, DK, CK, GK, GKFF, WK0, WOFF, DTX, BETA, WIDTH, PEN, REC,
-    SLOTS, CTRL, BLOCKCNT, SORTWORK, PERM, PF, NBUF
+    SLOTS, CTRL, BLOCKCNT, SORTWORK, PERM, PF, WT, AGG, NBUF
   };
   int device = -1;
   Buf bufs[NBUF];
+  survgpu::GraphCache graph;  // instantiated sweep graph of the last fit
 };
 
 namespace {
@@ -47,6 +49,7 @@ struct DevCtrl {
   unsigned pad[2];
   double out[survgpu::OUT_COUNT];
   unsigned long long timing[survgpu::PH_COUNT];
+  survgpu::GraphCtl gctl;
 };
 
 // Allocation failures map to SURV_E_NOMEM, anything else to SURV_E_CUDA.
@@ -90,6 +93,7 @@ int ensure(surv_workspace* ws, int id, size_t bytes, void** out) {
 }
 
 void free_all(surv_workspace* ws) {
+  survgpu::graph_cache_free(&ws->graph);
   for (auto& b : ws->bufs) {
     if (b.p) cudaFree(b.p);
     b.p = nullptr;
@@ -162,7 +166,7 @@ int fit_common(int model, const surv_data* d, const surv_opts* o_in, double* bet
   if (d->dtype != SURV_F32 && d->dtype != SURV_F64) { set_error("bad dtype"); return SURV_E_INVALID; }
   if (o.penalty < 0 || o.penalty > 2 || o.precision < 0 || o.precision > 1) { set_error("bad penalty/precision"); return SURV_E_INVALID; }
   if (!(o.lambda >= 0.0) || !std::isfinite(o.lambda) || !(o.tol >= 0.0) || o.max_sweeps < 0) { set_error("bad lambda/tol/max_sweeps"); return SURV_E_INVALID; }
-  if ((o.flags & ~SURV_FLAG_TEST_STALL) != 0) { set_error("unknown flags"); return SURV_E_INVALID; }
+  if ((o.flags & ~(SURV_FLAG_TEST_STALL | SURV_FLAG_PERSISTENT)) != 0) { set_error("unknown flags"); return SURV_E_INVALID; }
   if (single_j >= 0 && single_j >= p) { set_error("coordinate j=%d out of range", single_j); return SURV_E_INVALID; }
   if (n == 0) { set_error("no subjects"); return SURV_E_NO_EVENTS; }
   if (!d->time || !d->status) { set_error("null time/status"); return SURV_E_INVALID; }
@@ -185,8 +189,13 @@ int fit_common(int model, const surv_data* d, const surv_opts* o_in, double* bet
   const int M = model == SURV_COX ? 3 : 6;
   using W = surv_workspace;
 
+  // fits run as per-coordinate kernels replayed in a CUDA graph; the single
+  // evaluation of loglik_grad_hess, the stall test and SURV_FLAG_PERSISTENT
+  // use the persistent kernel
+  const bool graph = single_j < 0 && (o.flags & (SURV_FLAG_TEST_STALL | SURV_FLAG_PERSISTENT)) == 0;
   int G = 0, wpc = 0;
-  CUDA_TRY(survgpu::ccd_grid_size(model, layout, prec, &G, &wpc));
+  if (graph) CUDA_TRY(survgpu::graph_grid_size(model, layout, prec, &G, &wpc));
+  else CUDA_TRY(survgpu::ccd_grid_size(model, layout, prec, &G, &wpc));
   if (G < 1) { set_error("CCD kernel cannot be made co-resident"); return SURV_E_CUDA; }
   const int32_t nwarps = G * wpc;
   const int64_t nwords = (n + 31) / 32;
@@ -296,6 +305,10 @@ int fit_common(int model, const surv_data* d, const surv_opts* o_in, double* bet
   if ((rc = ensure(ws, W::PEN, 8 * (size_t)p, &pen))) return rc;
   const size_t slot_bytes = 4 * (size_t)survgpu::kSlotWords * 2 * G;
   if ((rc = ensure(ws, W::SLOTS, 2 * slot_bytes, &slots))) return rc;
+  void* wt = nullptr;
+  void* aggr = nullptr;
+  if (graph && (rc = ensure(ws, W::WT, 8 * (size_t)M * nwarps, &wt))) return rc;
+  if (graph && (rc = ensure(ws, W::AGG, 8 * (size_t)survgpu::kRep * M * G, &aggr))) return rc;
 
   CUDA_TRY(survgpu::prep_write_ends(time_p, n, static_cast<const int32_t*>(blockcnt), static_cast<int32_t*>(gend), s));
   CUDA_TRY(survgpu::prep_group_stats(static_cast<int32_t*>(gend), K, status_p, static_cast<int32_t*>(dk),
@@ -398,6 +411,11 @@ int fit_common(int model, const surv_data* d, const surv_opts* o_in, double* bet
   P.withhold_cta = (o.flags & SURV_FLAG_TEST_STALL) ? 0 : -1;
   P.epoch0 = 0;
   P.timeout_ns = (uint64_t)((o.wait_limit_s > 0.0 ? o.wait_limit_s : 2.0) * 1e9);
+  if (graph) {
+    P.wt = static_cast<uint64_t*>(wt);
+    P.agg = static_cast<uint64_t*>(aggr);
+    P.gctl = &ctrl->gctl;
+  }
   struct Events {
     cudaEvent_t a = nullptr, b = nullptr;
     ~Events() {
@@ -407,9 +425,19 @@ int fit_common(int model, const surv_data* d, const surv_opts* o_in, double* bet
   } ev;
   CUDA_TRY(cudaEventCreate(&ev.a));
   CUDA_TRY(cudaEventCreate(&ev.b));
-  CUDA_TRY(cudaEventRecord(ev.a, s));
-  CUDA_TRY(survgpu::launch_ccd(model, layout, prec, P, s));
-  ++launches;
+  int replays = 0;
+  if (graph) {
+    int glaunches = 0;
+    CUDA_TRY(survgpu::graph_init(P, s));
+    ++launches;
+    CUDA_TRY(survgpu::run_ccd_graph(model, layout, prec, P, s, o_in && o_in->workspace ? &ws->graph : nullptr,
+                                    ev.a, &replays, &glaunches));
+    launches += glaunches;
+  } else {
+    CUDA_TRY(cudaEventRecord(ev.a, s));
+    CUDA_TRY(survgpu::launch_ccd(model, layout, prec, P, s));
+    ++launches;
+  }
   CUDA_TRY(cudaEventRecord(ev.b, s));
   CUDA_TRY(cudaMemcpyAsync(&hc, ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, s));
   std::vector<double> beta_out(p);
@@ -438,8 +466,12 @@ int fit_common(int model, const surv_data* d, const surv_opts* o_in, double* bet
     info->eta_updates = (int64_t)hc.out[survgpu::OUT_ETA_UPDATES];
     info->kernel_launches = launches;
     info->ccd_kernel_ms = kernel_ms;
-    for (int i = 0; i < 12; ++i) info->phase_ms[i] = (double)hc.timing[i] * 1e-6;
+    for (int i = 0; i < 16; ++i) info->phase_ms[i] = (double)hc.timing[i] * 1e-6;
     info->phase_ms[survgpu::PH_PASS_SUM] /= (double)G;  // mean over CTAs
+  }
+  if (graph && hc.gctl.done != 1) {
+    set_error("CCD stopped after %d sweep replays without a stop decision", replays);
+    return SURV_E_CUDA;
   }
   if (hc.err != 0) {
     set_error("device-side wait expired (error word 0x%x)", hc.err);

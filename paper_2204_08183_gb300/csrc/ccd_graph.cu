@@ -1,0 +1,628 @@
+// Per-coordinate CCD schedule (Sections 2.4 and 2.7): two kernels per
+// coordinate, one sweep of them captured once as a CUDA graph and replayed
+// until the device reports that the fit has stopped.
+//
+//   k_pass(j)   CTA c reads the step of coordinate q = j - 1 (line c % kRep),
+//               each warp applies eta += x_q * step and e = exp(eta) to its
+//               own rows, then runs the row pass (step 2) of coordinate j
+//               over those rows and the CTA publishes its warp totals and its
+//               aggregate (the latter in kRep replicas).
+//   k_trans(j)  every CTA sums the aggregates of the CTAs before it (its
+//               exclusive prefix) in a fixed order, transforms its group ends
+//               (steps 3-4) and publishes three partial sums.  The last CTA
+//               to finish (atomic ticket; nobody waits for it) sums the
+//               partials in a fixed order, takes the FP64 Newton step of
+//               Section 2.4, stores beta_j and its trust-region width, on
+//               j = 0 evaluates the objective and the stopping rule, and
+//               publishes the step for k_pass(j + 1).
+//
+// Kernel boundaries order every producer before its consumers: no kernel
+// waits on another CTA.  A warp only reads and writes eta / e on its own
+// rows, so the update of q needs no barrier before the pass.  Launches use
+// programmatic dependent launch: loads of static tables are issued before
+// griddepcontrol.wait, which hides most of the launch gap.
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+
+#include "ccd_common.cuh"
+
+namespace survgpu {
+namespace {
+
+using namespace ccdk;
+
+// Pass kernel shape: 512 threads, two CTAs per SM (64 registers a thread):
+// tiles of 4 16-byte loads per array per lane (2 for Fine-Gray, whose six
+// running sums take the registers), 4 rounds of the column's nonzeros
+// prefetched.  Measured at N = 10^7 against one CTA of 16 warps per
+// SM, and against staging e in shared memory with bulk copies (whole SM or
+// per warp), this shape was the fastest.
+template <int MODEL, int LAYOUT>
+struct GCfg {
+  static constexpr int NT = 512;
+  static constexpr int MINB = 2;
+  static constexpr int U = MODEL == 1 ? 2 : 4;
+  static constexpr int SR = 4;
+};
+constexpr int kTransThreads = 256;
+constexpr int kTransWarps = kTransThreads / 32;
+
+// Programmatic dependent launch: everything before pdl_wait() may only read
+// data that no earlier kernel of the fit writes.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
+// Scalars of the control line a CTA reads (thread 0 loads them).
+struct LineView {
+  int stop = 0, nevals = 0;
+  double applied = 0.0;
+  ff delta = {0.f, 0.f};
+  double beta = 0.0, width = 0.0, pen = 0.0, dtx = 0.0, f_prev = 0.0;
+  long long passes = 0, eta_updates = 0;
+};
+__device__ __forceinline__ LineView load_line(const GraphCtl* ctl, int c) {
+  const CtlLine* L = &ctl->line[c % kRep];
+  LineView v;
+  v.stop = __ldcg(&L->stop);
+  v.nevals = __ldcg(&L->nevals);
+  v.applied = __ldcg(&L->applied);
+  v.delta = {__ldcg(&L->delta_hi), __ldcg(&L->delta_lo)};
+  v.beta = __ldcg(&L->beta);
+  v.width = __ldcg(&L->width);
+  v.pen = __ldcg(&L->pen);
+  v.dtx = __ldcg(&L->dtx);
+  v.f_prev = __ldcg(&L->f_prev);
+  v.passes = __ldcg(&L->passes);
+  v.eta_updates = __ldcg(&L->eta_updates);
+  return v;
+}
+
+// Fill every control line for the first coordinate of a fit.
+__global__ void k_graph_init(const __grid_constant__ CcdParams P) {
+  const int r = threadIdx.x;
+  if (r >= kRep) return;
+  CtlLine* L = &P.gctl->line[r];
+  L->stop = 0;
+  L->nevals = 0;
+  L->applied = 0.0;
+  L->delta_hi = 0.f;
+  L->delta_lo = 0.f;
+  L->beta = P.beta[0];
+  L->width = P.width[0];
+  L->pen = P.pen[0];
+  L->dtx = P.dTx[0];
+  L->f_prev = 0.0;
+  L->passes = 0;
+  L->eta_updates = 0;
+}
+
+template <int MODEL, int LAYOUT, typename T>
+__global__ void __launch_bounds__(GCfg<MODEL, LAYOUT>::NT, GCfg<MODEL, LAYOUT>::MINB)
+    k_pass(const __grid_constant__ CcdParams P, int j) {
+  using A = typename AccOf<T>::type;
+  using C = Cfg<MODEL, LAYOUT, T>;
+  constexpr int M = C::M;
+  __shared__ A s_wtot[kMaxWarpsPerCta][M];
+  __shared__ int s_stop;
+  __shared__ double s_applied;
+  __shared__ float s_delta[2];
+
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int w = tid >> 5;
+  const int WPC = P.wpc;
+  const int c = blockIdx.x;
+  const int G = P.G;
+  const int64_t n = P.n;
+  const int64_t nwords = (n + 31) >> 5;
+  const int gw = c * WPC + w;
+  const int64_t word_lo = min((int64_t)gw * P.wpw, nwords);
+  const int64_t word_hi = min(word_lo + P.wpw, nwords);
+  const int64_t row_lo = word_lo * 32;
+  const int64_t row_hi = min(word_hi * 32, n);
+  const int q = j == 0 ? P.p - 1 : j - 1;  // coordinate whose step is applied here
+
+  // column j's first nonzeros and the warp's group ends do not depend on
+  // earlier kernels: load them before waiting for the previous kernel
+  using GC = GCfg<MODEL, LAYOUT>;
+  PassPrefetch<T, GC::SR> pf;
+  pass_prefetch<LAYOUT, T, GC::SR>(P, j, gw, pf);
+  pdl_wait();
+
+  // the step of q (zero before the first coordinate of a fit), read once
+  if (tid == 0) {
+    const CtlLine* L = &P.gctl->line[c % kRep];
+    s_stop = __ldcg(&L->stop);
+    s_applied = __ldcg(&L->applied);
+    s_delta[0] = __ldcg(&L->delta_hi);
+    s_delta[1] = __ldcg(&L->delta_lo);
+  }
+  __syncthreads();
+  if (s_stop) return;  // the same value in every CTA
+  const double applied = s_applied;
+  if (applied != 0.0) warp_update<LAYOUT, T>(P, q, gw, row_lo, row_hi, applied, ff{s_delta[0], s_delta[1]});
+
+  // ------------------------------------------- step 2 for coordinate j
+  A* rec = reinterpret_cast<A*>(P.rec);
+  A tot[M];
+  warp_pass<MODEL, LAYOUT, T, GC::U, GC::SR>(P, j, row_lo, row_hi, rec, tot, pf);
+  pdl_launch_dependents();
+  if (lane == 0)
+#pragma unroll
+    for (int m = 0; m < M; ++m) s_wtot[w][m] = tot[m];
+  __syncthreads();
+  if (w == 0) {
+    // warp offsets inside the CTA (exclusive scan of the warp totals) and
+    // the CTA aggregate (their total), every lane in the same order
+    A v[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      acc_zero(v[m]);
+      if (lane < WPC) v[m] = s_wtot[lane][m];
+    }
+    warp_scan_n<M>(v, lane);
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      A ex = shfl_up(v[m], 1);
+      if (lane == 0) acc_zero(ex);
+      if (lane < WPC) P.wt[(size_t)m * P.nwarps + c * WPC + lane] = pack8(ex);
+      v[m] = shfl_idx(v[m], WPC - 1);
+    }
+    if (lane < kRep)
+#pragma unroll
+      for (int m = 0; m < M; ++m) P.agg[((size_t)lane * M + m) * G + c] = pack8(v[m]);
+  }
+}
+
+// Latency-bound: every load that does not depend on another value of this
+// kernel is issued first (CTA aggregates, this CTA's warp totals, its group
+// ends), the several sums of each stage share one reduction tree, and the
+// common path (at most one group end per thread) has one block barrier
+// before the partials.
+template <int MODEL, int LAYOUT, typename T>
+__global__ void __launch_bounds__(kTransThreads) k_trans(const __grid_constant__ CcdParams P, int j) {
+  using A = typename AccOf<T>::type;
+  constexpr int M = MODEL == 0 ? 3 : 6;
+  constexpr int NA = MODEL == 0 ? M : 2 * M;  // prefix sums (+ totals for Fine-Gray)
+  constexpr int NT = kTransThreads;
+  __shared__ A s_wp[kTransWarps][NA];
+  __shared__ A s_base[kMaxWarpsPerCta][M];
+  __shared__ A s_red[kTransWarps][3];
+  __shared__ int s_last;
+  __shared__ double s_lin[2];
+  __shared__ double s_next[4];
+
+  GraphCtl* ctl = P.gctl;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int w = tid >> 5;
+  const int WPC = P.wpc;
+  const int c = blockIdx.x;
+  const int G = P.G;
+  const bool eval = j == 0;
+  const int kc_lo = P.wk0[c * WPC], kc_hi = P.wk0[(c + 1) * WPC];
+  const int nends = kc_hi - kc_lo;
+  const bool one_end = nends <= NT;
+
+  // ---------------------------------------------- static loads
+  int kd = 0, kge = 0;
+  double kg = 0.0;
+  float2 kgf = make_float2(0.f, 0.f);
+  if (one_end && tid < nends) {
+    const int k = kc_lo + tid;
+    kd = P.dk[k];
+    kge = P.gend[k];
+    if (MODEL == 1) {
+      kg = P.Gk[k];
+      kgf = P.Gkff[k];
+    }
+  }
+  pdl_wait();
+
+  // ------------------ every load of this kernel's inputs, in one round trip
+  // (thread 0 also reads the control line: stop flag and the scalars of j)
+  LineView lv;
+  if (tid == 0) lv = load_line(ctl, c);
+  const uint64_t* agg = P.agg + (size_t)(c % kRep) * M * G;
+  // warp of this thread's group end (relative to the CTA); the pass kernel
+  // stored each warp's offset inside the CTA in wt
+  const int wl = (one_end && tid < nends) ? (int)((kge >> 5) / P.wpw) - c * WPC : (tid < WPC ? tid : 0);
+  uint64_t v0[M], v1[M], wbv[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    v0[m] = tid < G ? __ldcg(agg + (size_t)m * G + tid) : 0ull;
+    v1[m] = tid + NT < G ? __ldcg(agg + (size_t)m * G + tid + NT) : 0ull;
+    wbv[m] = ((one_end && tid < nends) || (!one_end && tid < WPC))
+                 ? __ldcg(P.wt + (size_t)m * P.nwarps + c * WPC + wl)
+                 : 0ull;
+  }
+  const A* rec = reinterpret_cast<const A*>(P.rec);
+  A kr[M];
+  if (one_end && tid < nends)
+#pragma unroll
+    for (int m = 0; m < M; ++m) kr[m] = rec[(size_t)(kc_lo + tid) * M + m];
+
+  // ------------------- per-warp sums of the aggregates of CTAs before c
+  {
+    A r[NA];
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      const A x0 = unpack8<A>(v0[m]), x1 = unpack8<A>(v1[m]);
+      acc_zero(r[m]);
+      if (tid < c) r[m] = x0;
+      if (tid + NT < c) r[m] = acc_add(r[m], x1);
+      if (MODEL == 1) r[M + (m % M)] = acc_add(x0, x1);
+    }
+    for (int qc = tid + 2 * NT; qc < G; qc += NT)  // grids above 512 CTAs
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        const A x = unpack8<A>(__ldcg(agg + (size_t)m * G + qc));
+        if (qc < c) r[m] = acc_add(r[m], x);
+        if (MODEL == 1) r[M + (m % M)] = acc_add(r[M + (m % M)], x);
+      }
+    warp_sum_n<NA>(r);
+    if (lane == 0)
+#pragma unroll
+      for (int i = 0; i < NA; ++i) s_wp[w][i] = r[i];
+  }
+  __syncthreads();
+  // prefix before CTA c and (Fine-Gray) grand totals, same order everywhere
+  A T_c[M], tot[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    T_c[m] = s_wp[0][m];
+    if (MODEL == 1) tot[m] = s_wp[0][M + (m % M)];
+  }
+#pragma unroll 1
+  for (int qw = 1; qw < kTransWarps; ++qw)
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      T_c[m] = acc_add(T_c[m], s_wp[qw][m]);
+      if (MODEL == 1) tot[m] = acc_add(tot[m], s_wp[qw][M + (m % M)]);
+    }
+
+  // ---------------------------------------------- steps 3-4
+  A fg1, fg2;
+  acc_zero(fg1);
+  acc_zero(fg2);
+  double pl = 0.0;
+  auto end_terms = [&](int d, const A (&Pm)[M], double g, float2 gf) {
+    A den = Pm[0], num1 = Pm[1], num2 = Pm[2];
+    if (MODEL == 1) {
+      const A gg = acc_base<A>(g, ff{gf.x, gf.y});
+      den = acc_add(den, acc_mul(gg, acc_add(tot[3 % M], acc_neg(Pm[3 % M]))));
+      num1 = acc_add(num1, acc_mul(gg, acc_add(tot[4 % M], acc_neg(Pm[4 % M]))));
+      num2 = acc_add(num2, acc_mul(gg, acc_add(tot[5 % M], acc_neg(Pm[5 % M]))));
+    }
+    const A inv = acc_recip(den);
+    const A Gr = acc_mul(num1, inv);
+    const A H = acc_mul(num2, inv);
+    fg1 = acc_add(fg1, acc_scale(Gr, d));
+    fg2 = acc_add(fg2, acc_scale(acc_add(H, acc_neg(acc_mul(Gr, Gr))), d));
+    if (eval) pl += (double)d * log(acc_to_d(den));
+  };
+  if (one_end) {
+    if (kd != 0) {
+      // prefix at the end: CTAs before, the CTA's warps before, the warp's rows
+      A Pm[M];
+#pragma unroll
+      for (int m = 0; m < M; ++m) Pm[m] = acc_add(acc_add(T_c[m], unpack8<A>(wbv[m])), kr[m]);
+      end_terms(kd, Pm, kg, kgf);
+    }
+  } else {
+    if (tid < WPC)
+#pragma unroll
+      for (int m = 0; m < M; ++m) s_base[tid][m] = acc_add(T_c[m], unpack8<A>(wbv[m]));
+    __syncthreads();
+    for (int k = kc_lo + tid; k < kc_hi; k += NT) {
+      const int d = P.dk[k];
+      if (d == 0) continue;
+      const int wl = (int)((P.gend[k] >> 5) / P.wpw) - c * WPC;
+      A Pm[M];
+#pragma unroll
+      for (int m = 0; m < M; ++m) Pm[m] = acc_add(s_base[wl][m], rec[(size_t)k * M + m]);
+      end_terms(d, Pm, MODEL == 1 ? P.Gk[k] : 0.0, MODEL == 1 ? P.Gkff[k] : make_float2(0.f, 0.f));
+    }
+  }
+
+  // ------------------------------------------- CTA partials, fixed order
+  {
+    A r[3] = {fg1, fg2, eval ? acc_from_d(pl, (A*)nullptr) : A{}};
+    warp_sum_n<3>(r);
+    if (lane == 0)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) s_red[w][i] = r[i];
+  }
+  __syncthreads();
+  uint64_t* part = reinterpret_cast<uint64_t*>(P.slot_part);
+  if (tid == 0) {
+    A a[3] = {s_red[0][0], s_red[0][1], s_red[0][2]};
+#pragma unroll 1
+    for (int qw = 1; qw < kTransWarps; ++qw)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) a[i] = acc_add(a[i], s_red[qw][i]);
+    if (lv.stop) {
+      s_last = 0;  // the fit has stopped: nothing to publish
+    } else {
+      part[c] = pack8(a[0]);
+      part[G + c] = pack8(a[1]);
+      part[2 * G + c] = pack8(a[2]);
+      // release: the partials above are visible to whoever sees the count
+      unsigned prev;
+      asm volatile("atom.add.release.gpu.u32 %0, [%1], 1;" : "=r"(prev) : "l"(&ctl->ticket) : "memory");
+      s_last = prev == (unsigned)(G - 1);
+    }
+  }
+  pdl_launch_dependents();
+  __syncthreads();
+  if (!s_last) return;
+
+  // ------------------------------- last CTA: the step of coordinate j
+  if (w < 3) {
+    // warp m sums partial vector m over the CTAs in a fixed order (acquire:
+    // every other CTA released its partials before its count)
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    A acc;
+    acc_zero(acc);
+    for (int q0 = 0; q0 < G; q0 += 32 * 10) {
+      uint64_t v[10];
+#pragma unroll
+      for (int u = 0; u < 10; ++u) {
+        const int qc = q0 + 32 * u + lane;
+        v[u] = qc < G ? __ldcg(part + (size_t)w * G + qc) : 0ull;
+      }
+#pragma unroll
+      for (int u = 0; u < 10; ++u) acc = acc_add(acc, unpack8<A>(v[u]));
+    }
+    A r[1] = {acc};
+    warp_sum_n<1>(r);
+    if (lane == 0) s_red[0][w] = r[0];
+  } else if (w == 3 && eval) {
+    // objective pieces at the current beta (every earlier step is stored)
+    double lin, pen;
+    warp_lin_pen(P, -1, 0.0, lin, pen);
+    if (lane == 0) {
+      s_lin[0] = lin;
+      s_lin[1] = pen;
+    }
+  } else if (w == 4 && lane == 0) {
+    // scalars of the next coordinate, for the control line
+    const int jn = j + 1 < P.p ? j + 1 : 0;
+    s_next[0] = __ldcg(P.beta + jn);
+    s_next[1] = __ldcg(P.width + jn);
+    s_next[2] = P.pen[jn];
+    s_next[3] = P.dTx[jn];
+  }
+  __syncthreads();
+  if (w == 0) {
+    LineView out;
+    if (lane == 0) {
+      out = lv;
+      const double grad = lv.dtx - acc_to_d(s_red[0][0]);  // l' = delta^T X_j - sum_k d_k G_k
+      const double hess = -acc_to_d(s_red[0][1]);           // l''
+      out.passes = lv.passes + 1;
+      out.applied = 0.0;
+      out.delta = {0.f, 0.f};
+      if (eval) {
+        // objective at the start of sweep s = nevals and the stopping rule
+        const int sidx = lv.nevals;
+        const double ll = s_lin[0] - acc_to_d(s_red[0][2]);
+        const double f = ll + s_lin[1];
+        const double fp = sidx >= 1 ? lv.f_prev : 0.0;
+        const bool conv = sidx >= 1 && fabs(f - fp) / fabs(f) < P.tol;
+        out.stop = (conv || sidx >= P.max_sweeps) ? 1 : 0;
+        out.nevals = sidx + 1;
+        out.f_prev = f;
+        if (out.stop) {
+          P.out[OUT_LOGLIK] = ll;
+          P.out[OUT_OBJECTIVE] = f;
+          P.out[OUT_OBJECTIVE_PREV] = fp;
+          P.out[OUT_SWEEPS] = (double)sidx;
+          P.out[OUT_CONVERGED] = conv ? 1.0 : 0.0;
+          P.out[OUT_ETA_UPDATES] = (double)lv.eta_updates;
+          P.out[OUT_PASSES] = (double)out.passes;
+          ctl->done = 1;
+        }
+      }
+      double bnew = lv.beta, wnew = lv.width;
+      if (!out.stop) {
+        const double step = newton_step(lv.beta, grad, hess, P.penalty, lv.pen);
+        if (step != 0.0) out.applied = copysign(fmin(fabs(step), lv.width), step);
+        bnew = lv.beta + out.applied;
+        wnew = fmax(2.0 * fabs(out.applied), lv.width / 2.0);
+        P.beta[j] = bnew;
+        P.width[j] = wnew;
+        if (out.applied != 0.0) out.eta_updates = lv.eta_updates + 1;
+        out.delta = d_to_ff(out.applied);
+      }
+      if (P.p == 1) {
+        out.beta = bnew;
+        out.width = wnew;
+      } else {
+        out.beta = s_next[0];
+        out.width = s_next[1];
+      }
+      out.pen = s_next[2];
+      out.dtx = s_next[3];
+      ctl->ticket = 0u;
+    }
+    // every lane writes one replica of the line
+    out.stop = __shfl_sync(0xffffffffu, out.stop, 0);
+    out.nevals = __shfl_sync(0xffffffffu, out.nevals, 0);
+    out.applied = __shfl_sync(0xffffffffu, out.applied, 0);
+    out.delta.hi = __shfl_sync(0xffffffffu, out.delta.hi, 0);
+    out.delta.lo = __shfl_sync(0xffffffffu, out.delta.lo, 0);
+    out.beta = __shfl_sync(0xffffffffu, out.beta, 0);
+    out.width = __shfl_sync(0xffffffffu, out.width, 0);
+    out.pen = __shfl_sync(0xffffffffu, out.pen, 0);
+    out.dtx = __shfl_sync(0xffffffffu, out.dtx, 0);
+    out.f_prev = __shfl_sync(0xffffffffu, out.f_prev, 0);
+    out.passes = __shfl_sync(0xffffffffu, out.passes, 0);
+    out.eta_updates = __shfl_sync(0xffffffffu, out.eta_updates, 0);
+    CtlLine* L = &ctl->line[lane];
+    L->stop = out.stop;
+    L->nevals = out.nevals;
+    L->applied = out.applied;
+    L->delta_hi = out.delta.hi;
+    L->delta_lo = out.delta.lo;
+    L->beta = out.beta;
+    L->width = out.width;
+    L->pen = out.pen;
+    L->dtx = out.dtx;
+    L->f_prev = out.f_prev;
+    L->passes = out.passes;
+    L->eta_updates = out.eta_updates;
+  }
+}
+
+// Grid of the pass kernel: as many CTAs per SM (up to MINB) as fit.
+template <int MODEL, int LAYOUT, typename T>
+cudaError_t grid_graph(int* G, int* wpc) {
+  using GC = GCfg<MODEL, LAYOUT>;
+  int dev = 0, sms = 0, occ = 0;
+  cudaError_t st = cudaGetDevice(&dev);
+  if (st != cudaSuccess) return st;
+  if ((st = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return st;
+  if ((st = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pass<MODEL, LAYOUT, T>, GC::NT, 0)) != cudaSuccess)
+    return st;
+  if (occ < 1) return cudaErrorLaunchOutOfResources;
+  *G = sms * std::min(occ, GC::MINB);
+  *wpc = GC::NT / 32;
+  return cudaSuccess;
+}
+
+template <int MODEL, int LAYOUT, typename T>
+cudaError_t capture_sweep(const CcdParams& P, bool pdl, cudaStream_t cs, cudaGraph_t* g) {
+  using GC = GCfg<MODEL, LAYOUT>;
+  cudaError_t st = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (st != cudaSuccess) return st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = pdl ? 1 : 0;
+  cudaLaunchConfig_t cp = {};
+  cp.gridDim = dim3(P.G);
+  cp.blockDim = dim3(GC::NT);
+  cp.stream = cs;
+  cp.attrs = attr;
+  cp.numAttrs = 1;
+  cudaLaunchConfig_t ct = cp;
+  ct.blockDim = dim3(kTransThreads);
+  cudaError_t lst = cudaSuccess;
+  for (int j = 0; j < P.p && lst == cudaSuccess; ++j) {
+    lst = cudaLaunchKernelEx(&cp, k_pass<MODEL, LAYOUT, T>, P, j);
+    if (lst == cudaSuccess) lst = cudaLaunchKernelEx(&ct, k_trans<MODEL, LAYOUT, T>, P, j);
+  }
+  st = cudaStreamEndCapture(cs, g);
+  return lst != cudaSuccess ? lst : st;
+}
+
+}  // namespace
+
+#define SURV_DISPATCH_G(FN, ...)                                             \
+  do {                                                                       \
+    if (model == 0 && layout == 0 && prec == 0) return FN<0, 0, float>(__VA_ARGS__);  \
+    if (model == 0 && layout == 0 && prec == 1) return FN<0, 0, double>(__VA_ARGS__); \
+    if (model == 0 && layout == 1 && prec == 0) return FN<0, 1, float>(__VA_ARGS__);  \
+    if (model == 0 && layout == 1 && prec == 1) return FN<0, 1, double>(__VA_ARGS__); \
+    if (model == 1 && layout == 0 && prec == 0) return FN<1, 0, float>(__VA_ARGS__);  \
+    if (model == 1 && layout == 0 && prec == 1) return FN<1, 0, double>(__VA_ARGS__); \
+    if (model == 1 && layout == 1 && prec == 0) return FN<1, 1, float>(__VA_ARGS__);  \
+    if (model == 1 && layout == 1 && prec == 1) return FN<1, 1, double>(__VA_ARGS__); \
+    return cudaErrorInvalidValue;                                            \
+  } while (0)
+
+namespace {
+cudaError_t capture_any(int model, int layout, int prec, const CcdParams& P, bool pdl, cudaStream_t cs,
+                        cudaGraph_t* g) {
+  SURV_DISPATCH_G(capture_sweep, P, pdl, cs, g);
+}
+}  // namespace
+
+cudaError_t graph_grid_size(int model, int layout, int prec, int* G, int* wpc) {
+  SURV_DISPATCH_G(grid_graph, G, wpc);
+}
+
+cudaError_t graph_init(const CcdParams& P, cudaStream_t s) {
+  k_graph_init<<<1, 32, 0, s>>>(P);
+  return cudaGetLastError();
+}
+
+void graph_cache_free(GraphCache* gc) {
+  if (!gc) return;
+  if (gc->exec) cudaGraphExecDestroy(gc->exec);
+  for (auto& e : gc->ev)
+    if (e) cudaEventDestroy(e);
+  if (gc->flag) cudaFreeHost(gc->flag);
+  if (gc->cs) cudaStreamDestroy(gc->cs);
+  *gc = GraphCache();
+}
+
+cudaError_t run_ccd_graph(int model, int layout, int prec, const CcdParams& P, cudaStream_t s, GraphCache* gc,
+                          cudaEvent_t t0, int* replays, int* launches) {
+  *replays = 0;
+  *launches = 0;
+  GraphCache local;
+  struct LocalGuard {
+    GraphCache* g;
+    ~LocalGuard() { graph_cache_free(g); }
+  } guard{gc ? nullptr : &local};
+  if (!gc) gc = &local;
+  cudaError_t st;
+  if (!gc->cs) {
+    if ((st = cudaStreamCreateWithFlags(&gc->cs, cudaStreamNonBlocking)) != cudaSuccess) return st;
+    for (auto& e : gc->ev)
+      if ((st = cudaEventCreateWithFlags(&e, cudaEventDisableTiming)) != cudaSuccess) return st;
+    if ((st = cudaMallocHost(&gc->flag, 2 * sizeof(int))) != cudaSuccess) return st;
+  }
+  // programmatic dependent launch between the kernels; SURVGPU_GRAPH_PDL=0
+  // turns it off (plain stream order), for comparison
+  const char* env = std::getenv("SURVGPU_GRAPH_PDL");
+  const bool pdl = !(env && env[0] == '0');
+  const int mlp = (model * 4 + layout * 2 + prec) * 2 + (pdl ? 1 : 0);
+  if (!gc->exec || gc->mlp != mlp || std::memcmp(&gc->key, &P, sizeof(P)) != 0) {
+    if (gc->exec) {
+      cudaGraphExecDestroy(gc->exec);
+      gc->exec = nullptr;
+    }
+    // capture on a private stream (the caller's may be the legacy stream)
+    cudaGraph_t g = nullptr;
+    st = capture_any(model, layout, prec, P, pdl, gc->cs, &g);
+    if (st == cudaSuccess) st = cudaGraphInstantiate(&gc->exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (st != cudaSuccess) {
+      gc->exec = nullptr;
+      return st;
+    }
+    gc->key = P;
+    gc->mlp = mlp;
+  }
+  gc->flag[0] = gc->flag[1] = 0;
+  if (t0 && (st = cudaEventRecord(t0, s)) != cudaSuccess) return st;
+  // One replay per sweep.  The stop flag of replay i is read while replay
+  // i + 1 runs; kernels of a replay after the stop return at once.  The
+  // device stops at the evaluation of sweep max_sweeps at the latest, which
+  // falls in replay max_sweeps.
+  const int max_replays = P.max_sweeps + 2;
+  int i = 0;
+  for (; i < max_replays; ++i) {
+    if ((st = cudaGraphLaunch(gc->exec, s)) != cudaSuccess) return st;
+    *launches += 2 * P.p;
+    if ((st = cudaMemcpyAsync(gc->flag + (i & 1), &P.gctl->done, sizeof(int), cudaMemcpyDeviceToHost, s)) !=
+        cudaSuccess)
+      return st;
+    if ((st = cudaEventRecord(gc->ev[i & 1], s)) != cudaSuccess) return st;
+    if (i >= 1) {
+      if ((st = cudaEventSynchronize(gc->ev[(i - 1) & 1])) != cudaSuccess) return st;
+      if (gc->flag[(i - 1) & 1]) {
+        ++i;
+        break;
+      }
+    }
+  }
+  *replays = i;
+  // the last replay's flag copy must land before the host buffer is reused
+  return cudaEventSynchronize(gc->ev[(i - 1) & 1]);
+}
+
+}  // namespace survgpu

@@ -106,6 +106,8 @@ __device__ __forceinline__ ff acc_add_v(ff a, float v) { return ff_add_f(a, v); 
 __device__ __forceinline__ double acc_add_v(double a, double v) { return a + v; }
 __device__ __forceinline__ double acc_to_d(ff a) { return ff_to_d(a); }
 __device__ __forceinline__ double acc_to_d(double a) { return a; }
+__device__ __forceinline__ ff acc_to_ff(ff a) { return a; }
+__device__ __forceinline__ ff acc_to_ff(double a) { return d_to_ff(a); }
 __device__ __forceinline__ ff acc_neg(ff a) { return ff_neg(a); }
 __device__ __forceinline__ double acc_neg(double a) { return -a; }
 
@@ -122,23 +124,163 @@ __device__ __forceinline__ ff shfl_idx(ff a, int s) {
 }
 __device__ __forceinline__ double shfl_idx(double a, int s) { return __shfl_sync(0xffffffffu, a, s); }
 
-// Fixed-shape tree reduction over the 32 lanes (result valid in lane 0 and
-// broadcast to all lanes).  The order of additions does not depend on timing.
-template <typename A>
-__device__ __forceinline__ A warp_sum(A v) {
+// Fixed-shape tree reduction over the 32 lanes (result broadcast to all
+// lanes).  The order of additions does not depend on timing.  The bodies are
+// out of line: the kernels call them from dozens of sites, and inlining every
+// copy made the once-per-coordinate code outgrow the SM's instruction cache.
+static __device__ __noinline__ ff warp_sum_ff(ff v) {
 #pragma unroll
-  for (int d = 16; d > 0; d >>= 1) v = acc_add(v, shfl_down(v, d));
+  for (int d = 16; d > 0; d >>= 1) v = ff_add(v, shfl_down(v, d));
   return shfl_idx(v, 0);
+}
+static __device__ __noinline__ double warp_sum_dd(double v) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
+  return __shfl_sync(0xffffffffu, v, 0);
+}
+__device__ __forceinline__ ff warp_sum(ff v) { return warp_sum_ff(v); }
+__device__ __forceinline__ double warp_sum(double v) { return warp_sum_dd(v); }
+
+// N independent sums with the same tree shape as warp_sum, interleaved
+// level by level so that their shuffles and adds overlap (inline; for the
+// latency-bound once-per-coordinate code).  Results broadcast to all lanes.
+template <int N>
+__device__ __forceinline__ void warp_sum_n(ff (&v)[N]) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    ff u[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) u[i] = shfl_down(v[i], d);
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = ff_add(v[i], u[i]);
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i) v[i] = shfl_idx(v[i], 0);
+}
+template <int N>
+__device__ __forceinline__ void warp_sum_n(double (&v)[N]) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    double u[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) u[i] = __shfl_down_sync(0xffffffffu, v[i], d);
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] += u[i];
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i) v[i] = __shfl_sync(0xffffffffu, v[i], 0);
+}
+
+// The same sums where register pressure matters: interleaved up to three
+// at a time, one out-of-line tree each beyond that (identical results).
+template <int N, typename A>
+__device__ __forceinline__ void warp_sum_some(A (&v)[N]) {
+  if constexpr (N <= 3) {
+    warp_sum_n<N>(v);
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = warp_sum(v[i]);
+  }
+}
+
+// N independent inclusive scans over the lanes (Hillis-Steele, fixed
+// shape), interleaved level by level.
+template <int N>
+__device__ __forceinline__ void warp_scan_n(ff (&v)[N], int lane) {
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    ff u[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) u[i] = shfl_up(v[i], d);
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+      if (lane >= d) v[i] = ff_add(v[i], u[i]);
+  }
+}
+template <int N>
+__device__ __forceinline__ void warp_scan_n(double (&v)[N], int lane) {
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    double u[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) u[i] = __shfl_up_sync(0xffffffffu, v[i], d);
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+      if (lane >= d) v[i] += u[i];
+  }
 }
 
 // Inclusive scan over lanes (Hillis-Steele, fixed shape).
-template <typename A>
-__device__ __forceinline__ A warp_inclusive_scan(A v, int lane) {
+static __device__ __noinline__ ff warp_scan_ff(ff v, int lane) {
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
-    A u = shfl_up(v, d);
-    if (lane >= d) v = acc_add(v, u);
+    ff u = shfl_up(v, d);
+    if (lane >= d) v = ff_add(v, u);
   }
+  return v;
+}
+static __device__ __noinline__ double warp_scan_dd(double v, int lane) {
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    double u = __shfl_up_sync(0xffffffffu, v, d);
+    if (lane >= d) v += u;
+  }
+  return v;
+}
+__device__ __forceinline__ ff warp_inclusive_scan(ff v, int lane) { return warp_scan_ff(v, lane); }
+__device__ __forceinline__ double warp_inclusive_scan(double v, int lane) { return warp_scan_dd(v, lane); }
+
+// ------------------------------------------------------ L2 cache policies
+// e (and W) are re-read by every coordinate's pass and should stay in L2;
+// column data is read once per sweep and should not push them out.
+__device__ __forceinline__ uint64_t l2_keep() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t l2_stream() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+// Loads with an L2 policy.  The "memory" clobber keeps loads of data this
+// warp has just written (e after the update) behind those writes.
+__device__ __forceinline__ void ld4_hint(const float* p, uint64_t pol, float (&v)[4]) {
+  asm volatile("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3])
+               : "l"(p), "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ void ld4_hint(const double* p, uint64_t pol, double (&v)[2]) {
+  asm volatile("ld.global.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"
+               : "=d"(v[0]), "=d"(v[1])
+               : "l"(p), "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ float ld_hint(const float* p, uint64_t pol) {
+  float v;
+  asm volatile("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol) : "memory");
+  return v;
+}
+__device__ __forceinline__ double ld_hint(const double* p, uint64_t pol) {
+  double v;
+  asm volatile("ld.global.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol) : "memory");
+  return v;
+}
+__device__ __forceinline__ int ld_hint(const int* p, uint64_t pol) {
+  int v;
+  asm("ld.global.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+  return v;
+}
+// column data (never written while a fit runs): no ordering needed
+__device__ __forceinline__ float ld_stream(const float* p, uint64_t pol) {
+  float v;
+  asm("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ double ld_stream(const double* p, uint64_t pol) {
+  double v;
+  asm("ld.global.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
   return v;
 }
 
@@ -165,32 +307,5 @@ enum : unsigned {
   DEV_ERR_TIMEOUT = 1u,      // a grid exchange wait gave up
   DEV_ERR_ABORT = 2u,        // a test-only abort request was honoured
 };
-
-// Wait (one warp) until the epoch word of every slot 0..count-1 equals or
-// exceeds `epoch`.  Slots are `stride` words apart, the epoch sits at word
-// `eoff` of each slot.  Gives up after `limit_ns` (sets DEV_ERR_TIMEOUT) or
-// as soon as another block has raised an error.  Returns true on success
-// (same value in all lanes).
-__device__ __forceinline__ bool warp_wait_epochs(const unsigned* slots, int count, int stride, int eoff,
-                                                 unsigned epoch, unsigned* err, uint64_t limit_ns) {
-  const int lane = threadIdx.x & 31;
-  bool ok = true;
-  uint64_t t0 = 0;
-  bool timed = false;
-  for (int q = lane; q < count; q += 32) {
-    const unsigned* f = slots + (size_t)q * stride + eoff;
-    while (ld_acquire(f) < epoch) {
-      if (ld_volatile(err) != 0u) { ok = false; break; }
-      if (!timed) { t0 = global_ns(); timed = true; }
-      if (global_ns() - t0 > limit_ns) {
-        atomicOr(err, DEV_ERR_TIMEOUT);
-        ok = false;
-        break;
-      }
-    }
-    if (!ok) break;
-  }
-  return __all_sync(0xffffffffu, ok);
-}
 
 }  // namespace survgpu

@@ -65,6 +65,40 @@ struct CcdParams {
   int32_t withhold_cta;  // test knob: this CTA never publishes (-1 = off)
   unsigned epoch0;       // unused (counters restart at 0 every launch)
   uint64_t timeout_ns;   // bound on every grid-exchange wait
+
+  // per-coordinate kernel pair only (null for the persistent kernel)
+  uint64_t* wt;          // [M][nwarps] warp totals of the last pass (8-byte payload words)
+  uint64_t* agg;         // [kRep][M][G] CTA aggregates of the last pass, replicated
+  struct GraphCtl* gctl; // fit state carried between kernels
+};
+
+// Fit state of the per-coordinate kernel pair.  The last transform CTA of
+// each coordinate j (found with an atomic ticket) owns the scalar state: it
+// takes the Newton step, stores beta_j and its width, decides convergence on
+// j = 0, and publishes in kRep identical 128-byte lines everything the next
+// two kernels need (the step, and the scalars of coordinate j + 1).  CTA c of
+// a kernel reads line c % kRep once, so no line has more than a handful of
+// readers.
+constexpr int kRep = 32;
+struct alignas(128) CtlLine {
+  int32_t stop;          // the fit has stopped: every later kernel returns
+  int32_t nevals;        // objective evaluations so far (one per sweep)
+  double applied;        // step applied to the coordinate just finished
+  float delta_hi;        // the same step as float-float
+  float delta_lo;
+  double beta;           // beta, trust-region width, lambda * penalty factor
+  double width;          //   and delta^T X of the next coordinate
+  double pen;
+  double dtx;
+  double f_prev;         // objective at the latest evaluation
+  long long passes;      // coordinate passes so far
+  long long eta_updates; // nonzero steps so far
+  char pad[128 - 88];
+};
+struct GraphCtl {
+  CtlLine line[kRep];
+  int32_t done;          // host-visible copy of stop
+  uint32_t ticket;       // transform CTAs finished in the current kernel
 };
 
 // Phase times accumulated by thread 0 of CTA 0 (ns), plus statistics of the
@@ -82,6 +116,10 @@ enum PhaseIndex : int {
   PH_PASS_MAX = 9,    // largest total pass time of any CTA
   PH_PASS_MIN = 10,   // smallest total pass time of any CTA
   PH_PASS_SUM = 11,   // sum over CTAs of the total pass time
+  PH_DENSE_MAX = 12,  // largest total time of the dense part of the pass (any CTA)
+  PH_SPARSE_MAX = 13, // largest total time of the sparse part (any CTA)
+  PH_EX1_SUMS = 14,   // CTA 0: warp sums before the exchange #1 payload
+  PH_EX1_STORE = 15,  // CTA 0: payload stores before the arrival
   PH_COUNT = 16,
 };
 
@@ -104,6 +142,28 @@ enum OutIndex : int {
 cudaError_t launch_ccd(int model, int layout, int prec, const CcdParams& P, cudaStream_t s);
 // Co-resident CTAs and warps per CTA of the CCD kernel for this configuration.
 cudaError_t ccd_grid_size(int model, int layout, int prec, int* G, int* wpc);
+
+// Per-coordinate schedule (ccd_graph.cu): grid of the pass / transform
+// kernels, and a fit that replays one captured sweep (2p kernels) until the
+// device reports that the fit has stopped.  P.gctl and P.wt must be set and
+// *P.gctl zeroed; at most max_sweeps + 2 sweeps are replayed.
+// The instantiated sweep graph is kept in a GraphCache (one per workspace)
+// and reused while the parameters are byte-identical; t0 (optional) is
+// recorded on s right before the first replay.
+struct GraphCache {
+  cudaGraphExec_t exec = nullptr;
+  CcdParams key;
+  int mlp = -1;
+  cudaStream_t cs = nullptr;     // capture stream
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  int* flag = nullptr;           // pinned [2]: stop flag of the last two replays
+};
+cudaError_t graph_grid_size(int model, int layout, int prec, int* G, int* wpc);
+// Fill the control lines for the first coordinate of a fit (P.gctl zeroed).
+cudaError_t graph_init(const CcdParams& P, cudaStream_t s);
+cudaError_t run_ccd_graph(int model, int layout, int prec, const CcdParams& P, cudaStream_t s, GraphCache* gc,
+                          cudaEvent_t t0, int* replays, int* launches);
+void graph_cache_free(GraphCache* gc);
 
 // ---- prep kernels (prep.cu) --------------------------------------------
 cudaError_t prep_check_times(const int32_t* time, const int8_t* status, int64_t n, int model,

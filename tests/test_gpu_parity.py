@@ -152,10 +152,14 @@ def test_deterministic(lib):
 
 
 # ------------------------------------------------------------ full fits
-def _fit_check(model, d, penalty, lam, prec, beta_tol=1e-5, tol=1e-10, where="device"):
+SCHEDULES = {"graph": 0, "persistent": binding.SURV_FLAG_PERSISTENT}
+
+
+def _fit_check(model, d, penalty, lam, prec, beta_tol=1e-5, tol=1e-10, where="device", schedule="graph"):
     sd = survdata(d, where)
     fn = binding.cox_fit if model == "cox" else binding.fg_fit
-    beta, info, rc = fn(sd, penalty=penalty, lam=lam, tol=tol, max_sweeps=500, precision=prec)
+    beta, info, rc = fn(sd, penalty=penalty, lam=lam, tol=tol, max_sweeps=500, precision=prec,
+                        flags=SCHEDULES[schedule])
     X = oracle_X(d)
     st = d["status"] if model == "fg" else np.where(d["status"] == 2, 0, d["status"]).astype(np.int8)
     ref = oracle.ccd_fit(model, d["time"], st, X, penalty, lam, tol=tol, max_sweeps=500)
@@ -183,19 +187,64 @@ def test_fit_dense_cox_l2_config1_shape(lib, prec):
     _fit_check("cox", d, "l2", 1.0, prec, tol=1e-8)
 
 
+@pytest.mark.parametrize("schedule", ["graph", "persistent"])
 @pytest.mark.parametrize("prec", ["f32c", "f64"])
-def test_fit_csc_cox_l1(lib, prec):
+def test_fit_csc_cox_l1(lib, prec, schedule):
     d = synth.cohort_cox_sparse(60_000, 20, seed=2, density=0.05, n_true=4, laplace_scale=0.5, grid=3650)
     if prec == "f64":
         d["values"] = d["values"].astype(np.float64)
     lmax = oracle.lambda_max("cox", d["time"], d["status"], oracle_X(d))
-    _fit_check("cox", d, "l1", 0.2 * lmax, prec)
+    _fit_check("cox", d, "l1", 0.2 * lmax, prec, schedule=schedule)
 
 
+@pytest.mark.parametrize("schedule", ["graph", "persistent"])
 @pytest.mark.parametrize("prec", ["f32c", "f64"])
-def test_fit_fg_dense_l2(lib, prec):
+def test_fit_fg_dense_l2(lib, prec, schedule):
     d = synth.cohort_fg_dense(30_000, 6, seed=3, grid=1000, n_true=4, dtype=np.float32 if prec == "f32c" else np.float64)
-    _fit_check("fg", d, "l2", 10.0, prec)
+    _fit_check("fg", d, "l2", 10.0, prec, schedule=schedule)
+
+
+@pytest.mark.parametrize("schedule", ["graph", "persistent"])
+def test_fit_fg_csc_l1(lib, schedule):
+    d = small_csc(40_000, 10, seed=16, density=0.08, n_times=800, competing=0.25)
+    lmax = oracle.lambda_max("fg", d["time"], d["status"], oracle_X(d))
+    _fit_check("fg", d, "l1", 0.25 * lmax, "f32c", schedule=schedule)
+
+
+@pytest.mark.parametrize("kind", ["heavy_ties", "near_unique_times"])
+def test_fit_csc_cox_staged_pass(lib, kind):
+    # Millions of rows: every warp of the pass kernel owns more than one tile,
+    # so e is staged in shared memory and walked lane by lane.  Near-unique
+    # times put hundreds of group ends in each warp (more than 32 of them,
+    # and more than two in one lane).
+    if kind == "heavy_ties":
+        d = synth.cohort_cox_sparse(3_000_000, 5, seed=31, density=0.05, n_true=3, laplace_scale=0.5, grid=3650)
+    else:
+        d = small_csc(2_000_000, 4, seed=32, density=0.05, n_times=1_500_000)
+    lmax = oracle.lambda_max("cox", d["time"], np.where(d["status"] == 2, 0, d["status"]).astype(np.int8),
+                             oracle_X(d))
+    _fit_check("cox", d, "l1", 0.2 * lmax, "f32c", tol=1e-9)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_fit_few_coordinates(lib, p):
+    # p = 1 folds the finish of a coordinate and the objective evaluation
+    # into the same kernel of the next sweep; p = 2, 3 cover the wrap-around
+    d = synth.cohort_cox_dense(8_000, p, seed=40 + p, n_true=p, grid=150)
+    _fit_check("cox", d, "l2", 2.0, "f32c", tol=1e-9)
+
+
+def test_fit_graph_reuse_in_workspace(lib):
+    # the second fit in a workspace replays the cached graph; a third with
+    # another lambda captures a new one
+    d = synth.cohort_cox_sparse(40_000, 9, seed=17, density=0.05, n_true=3, laplace_scale=0.5, grid=900)
+    sd = survdata(d)
+    ws = binding.Workspace()
+    lmax = oracle.lambda_max("cox", d["time"], d["status"], oracle_X(d))
+    runs = [binding.cox_fit(sd, penalty="l1", lam=lam * lmax, tol=1e-10, workspace=ws) for lam in (0.3, 0.3, 0.1)]
+    assert np.array_equal(runs[0][0], runs[1][0]) and runs[0][1]["sweeps"] == runs[1][1]["sweeps"]
+    ref = oracle.ccd_fit("cox", d["time"], d["status"], oracle_X(d), "l1", 0.1 * lmax, tol=1e-10, max_sweeps=500)
+    np.testing.assert_allclose(runs[2][0], ref["beta"], atol=1e-5)
 
 
 def test_fit_fg_csc_l1_host_buffers(lib):
@@ -220,10 +269,18 @@ def test_lambda_max_gives_zero(lib):
     assert np.all(beta == 0.0) and info["eta_updates"] == 0
 
 
-def test_max_sweeps_reports_not_converged(lib):
+@pytest.mark.parametrize("schedule", ["graph", "persistent"])
+def test_max_sweeps_reports_not_converged(lib, schedule):
     d = synth.cohort_cox_dense(3_000, 5, seed=9, n_true=4, grid=100)
-    beta, info, rc = binding.cox_fit(survdata(d), penalty="l2", lam=1.0, tol=0.0, max_sweeps=3)
+    beta, info, rc = binding.cox_fit(survdata(d), penalty="l2", lam=1.0, tol=0.0, max_sweeps=3,
+                                     flags=SCHEDULES[schedule])
     assert rc == binding.SURV_W_NOT_CONVERGED and info["sweeps"] == 3 and info["converged"] == 0
     ref = oracle.ccd_fit("cox", d["time"], d["status"], d["X"], "l2", 1.0, tol=0.0, max_sweeps=3)
     np.testing.assert_allclose(beta, ref["beta"], atol=1e-7)
     assert info["coordinate_passes"] == 3 * 5 + 1
+    b0 = np.full(5, 0.05)
+    beta, info, rc = binding.cox_fit(survdata(d), beta=b0.copy(), penalty="l2", lam=1.0, tol=0.0, max_sweeps=0,
+                                     flags=SCHEDULES[schedule])
+    assert rc == binding.SURV_W_NOT_CONVERGED and info["sweeps"] == 0 and np.array_equal(beta, b0)
+    ref = oracle.ccd_fit("cox", d["time"], d["status"], d["X"], "l2", 1.0, tol=0.0, max_sweeps=0, beta0=b0)
+    assert abs(info["objective"] - ref["objective"]) <= 1e-6 * abs(ref["objective"])
