@@ -197,7 +197,11 @@ def run_gpu(args, rank, world):
         t_max, sweeps_all = float(tt.item()), float(ss.item())
     value = sweeps_all / (t_max / 1e3)
 
-    # roofline of the dominant kernel (the persistent CCD kernel)
+    # Roofline of the dominant kernel.  The unit of work is one coordinate:
+    # the k_pass + k_trans pair (graph schedule) that reads e over all N rows
+    # and the column's CSC slice; its duration is the fit's CCD device time
+    # (all graph replays, kernel gaps included) divided by the coordinate
+    # passes.  Eta updates after nonzero steps are counted in the bytes.
     nnz = int(d["col_ptr"][-1])
     K = infos[-1]["n_groups"]
     passes = sum(i["coordinate_passes"] for i in infos)
@@ -213,23 +217,33 @@ def run_gpu(args, rank, world):
         pass
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = alg_bytes / (kern_ms / 1e3) / 1e9
+    us_per_coord = kern_ms * 1e3 / passes
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)" if peaks else "fallback 6800 GB/s",
-                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
-                "kernel": ("ccd_kernel<cox,csc,f32> (persistent, one launch per fit)" if args.schedule == "persistent"
-                           else "k_pass + k_trans <cox,csc,f32> per coordinate, one graph replay per sweep; "
-                                "time = all replays of a fit"),
-                "algorithmic_bytes_per_launch": alg_bytes / len(infos),
-                "kernel_ms_per_launch": kern_ms / len(infos),
-                "per_pass_bytes": per_pass, "passes_per_launch": passes / len(infos),
-                "eta_updates_per_launch": upd / len(infos)}
+                "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "unit_of_work": "one coordinate (row pass + transform/Newton)",
+                "algorithmic_bytes_per_coordinate": round(alg_bytes / passes),
+                "us_per_coordinate": round(us_per_coord, 3),
+                "passes_per_fit": passes / len(infos), "eta_updates_per_fit": upd / len(infos)}
+    if args.schedule == "graph" and n == 10_000_000 and p == 100:
+        # dram__bytes_read.sum + dram__bytes_write.sum of k_pass + k_trans per
+        # coordinate, steady state (ncu --cache-control none, one pass); see
+        # profiles/k_pass_k_trans_cox_csc_n1e7.md.  e stays in L2 across
+        # coordinates; DRAM sees the column slice and the eta / e writes.
+        roofline["traffic"] = round(0.5 * ((4129792 + 3532032 + 56320 + 3584) + (4101120 + 191232 + 256 + 3328)))
+        roofline["traffic_note"] = "bytes per coordinate, ncu steady-state capture of the kernels as committed"
+    else:
+        roofline["traffic"] = None
+    roofline["kernel"] = ("ccd_kernel<cox,csc,f32> (persistent, one launch per fit)" if args.schedule == "persistent"
+                          else "k_pass + k_trans <cox,csc,f32>, one pair per coordinate, one graph replay per sweep")
     if args.schedule == "persistent":
         roofline["phase_ms_per_launch"] = {k: round(sum(i["phase_ms"][q] for i in infos) / len(infos), 4)
-                                        for q, k in enumerate(["pass_cta0", "ex1_arrive", "ex1_wait", "ex1_after",
-                                                               "transform", "ex2_arrive", "ex2_wait",
-                                                               "ex2_newton", "update", "pass_max_cta",
-                                                               "pass_min_cta", "pass_mean_cta", "dense_max_cta",
-                                                               "sparse_max_cta", "ex1_sums", "ex1_stores"])}
+                                           for q, k in enumerate(["pass_cta0", "ex1_arrive", "ex1_wait",
+                                                                  "ex1_after", "transform", "ex2_arrive",
+                                                                  "ex2_wait", "ex2_newton", "update",
+                                                                  "pass_max_cta", "pass_min_cta",
+                                                                  "pass_mean_cta", "dense_max_cta",
+                                                                  "sparse_max_cta", "ex1_sums", "ex1_stores"])}
 
     out = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 3), "higher_is_better": True,
