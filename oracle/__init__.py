@@ -12,3 +12,4 @@ the paper by eye.  Every function cites the passage it follows.
 Parity status of each function is listed in ``oracle/survival.py``'s header.
 """
 from .survival import *  # noqa: F401,F403
+from .nll import *  # noqa: F401,F403
