@@ -236,6 +236,41 @@ int surv_groups(const int32_t *time, const int8_t *status, int64_t n, int64_t ma
 int loglik_grad_hess_noalloc(const surv_data *data, int32_t model, const double *beta, int32_t j,
                              double *loglik, double *grad, double *hess, int32_t precision, void *stream);
 
+/* ---- differentiable form ------------------------------------------------
+ * The Cox negative log partial likelihood (Breslow ties, Section 2.9 with
+ * the risk-set sums of Section 2.7) of C linear predictors at once,
+ * eta = X B:
+ *   NLL_b = - sum_i delta_i eta_ib + sum_k d_k log sum_{r <= e_k} exp(eta_rb),
+ * delta_i = (status_i == 1), subjects in non-increasing time, and its
+ * gradient dNLL/dB = X^T (exp(eta) * Lambda - delta), Lambda_b(i) the sum of
+ * d_k / den_kb over the tie groups whose risk set holds i.
+ *
+ * X is bfloat16, row-major n x p; B float32 row-major p x C.  X B runs on
+ * the tensor cores (bf16 inputs, FP32 accumulation) with B split into a
+ * bf16 high and low part, so eta carries about 16 significant bits of B;
+ * the risk-set scans use FP32 values with float-float running sums and the
+ * logs are FP64.  All arrays are device memory; C <= 64. */
+typedef struct surv_nll_data {
+  int64_t n;                     /* subjects                                       */
+  int32_t p;                     /* covariates (columns of X)                      */
+  int32_t ncols;                 /* C: linear predictors (columns of B), 1..64     */
+  const int32_t *time;           /* [n] non-increasing                              */
+  const int8_t *status;          /* [n] 0 censored, 1 event (2 counts as censored)   */
+  const void *X;                 /* [n][p] bfloat16, row-major                       */
+} surv_nll_data;
+
+/* nll[C] (device doubles) at B [p][C] (device floats).  Keeps eta and the
+ * risk-set sums in the workspace `ws` (required) for cox_nll_backward.
+ * Errors: SURV_E_INVALID (null, sizes, host pointers), SURV_E_UNSORTED,
+ * SURV_E_STATUS, SURV_E_NOMEM, SURV_E_CUDA. */
+int cox_nll_forward(const surv_nll_data *data, const float *B, double *nll, void *stream, surv_workspace *ws);
+
+/* grad_B [p][C] (device floats) = sum_b grad_nll[b] dNLL_b/dB at the B of
+ * the last cox_nll_forward on the same workspace and data (SURV_E_INVALID
+ * otherwise).  grad_nll [C] device doubles (the incoming gradient). */
+int cox_nll_backward(const surv_nll_data *data, const double *grad_nll, float *grad_B, void *stream,
+                     surv_workspace *ws);
+
 /* Short name of a return code (static string). */
 const char *surv_strerror(int code);
 

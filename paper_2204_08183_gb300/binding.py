@@ -42,13 +42,18 @@ SURV_FLAG_PERSISTENT = 2
 # exported symbols, in the order the header declares them
 EXPORTS = ["surv_opts_default", "surv_workspace_create", "surv_workspace_destroy", "surv_sort_desc",
            "cox_fit", "fg_fit", "loglik_grad_hess", "surv_groups", "loglik_grad_hess_noalloc",
-           "surv_strerror", "surv_last_error", "surv_version"]
+           "cox_nll_forward", "cox_nll_backward", "surv_strerror", "surv_last_error", "surv_version"]
 
 
 class surv_data(C.Structure):
     _fields_ = [("n", C.c_int64), ("p", C.c_int64), ("time", C.c_void_p), ("status", C.c_void_p),
                 ("layout", C.c_int32), ("dtype", C.c_int32), ("col_ptr", C.c_void_p), ("row_idx", C.c_void_p),
                 ("values", C.c_void_p)]
+
+
+class surv_nll_data(C.Structure):
+    _fields_ = [("n", C.c_int64), ("p", C.c_int32), ("ncols", C.c_int32), ("time", C.c_void_p),
+                ("status", C.c_void_p), ("X", C.c_void_p)]
 
 
 class surv_opts(C.Structure):
@@ -98,6 +103,9 @@ def load(path: str = LIB_PATH):
     lib.loglik_grad_hess_noalloc.argtypes = [C.POINTER(surv_data), C.c_int32, C.c_void_p, C.c_int32,
                                              C.POINTER(C.c_double), C.POINTER(C.c_double),
                                              C.POINTER(C.c_double), C.c_int32, C.c_void_p]
+    for f in (lib.cox_nll_forward, lib.cox_nll_backward):
+        f.argtypes = [C.POINTER(surv_nll_data), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        f.restype = C.c_int
     lib.surv_strerror.argtypes = [C.c_int]
     lib.surv_strerror.restype = C.c_char_p
     lib.surv_last_error.restype = C.c_char_p
@@ -313,3 +321,69 @@ def surv_groups(time, status, stream=None):
 
 def strerror(code: int) -> str:
     return load().surv_strerror(code).decode()
+
+
+# ----------------------------------------------------------- differentiable form
+def _nll_data(X, time, status, ncols):
+    n, p = int(X.shape[0]), int(X.shape[1])
+    return surv_nll_data(n, p, int(ncols), C.c_void_p(_ptr(time)), C.c_void_p(_ptr(status)), C.c_void_p(_ptr(X)))
+
+
+def cox_nll_forward(X, time, status, B, workspace, stream=None):
+    """NLL per column of B (float64, device) through cox_nll_forward.  X:
+    bfloat16 (n, p) row-major; B: float32 (p, C); time int32, status int8,
+    all CUDA tensors."""
+    import torch
+    nll = torch.empty(int(B.shape[1]), dtype=torch.float64, device=B.device)
+    d = _nll_data(X, time, status, B.shape[1])
+    _check(load().cox_nll_forward(C.byref(d), C.c_void_p(_ptr(B)), C.c_void_p(_ptr(nll)), _stream(stream),
+                                  workspace.handle))
+    return nll
+
+
+def cox_nll_backward(X, time, status, grad_nll, ncols, workspace, stream=None):
+    """dNLL/dB weighted by grad_nll (float64 [C], device) at the B of the
+    last cox_nll_forward on `workspace`; float32 (p, C)."""
+    import torch
+    gB = torch.empty((int(X.shape[1]), int(ncols)), dtype=torch.float32, device=grad_nll.device)
+    d = _nll_data(X, time, status, ncols)
+    _check(load().cox_nll_backward(C.byref(d), C.c_void_p(_ptr(grad_nll)), C.c_void_p(_ptr(gB)), _stream(stream),
+                                   workspace.handle))
+    return gB
+
+
+def _cox_nll_function():
+    import torch
+
+    class CoxNLL(torch.autograd.Function):
+        """NLL_b(eta = X B) per column b as a differentiable function of B
+        (X bfloat16 (n, p), time int32 and status int8 sorted by decreasing
+        time, all on the GPU).  Forward and backward run in libsurvgpu; each
+        forward keeps its own workspace for its backward."""
+
+        @staticmethod
+        def forward(ctx, B, X, time, status):
+            B = B.contiguous()
+            ws = Workspace()
+            nll = cox_nll_forward(X, time, status, B, ws)
+            ctx.ws, ctx.X, ctx.time, ctx.status, ctx.ncols = ws, X, time, status, int(B.shape[1])
+            return nll
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            g = grad_out.detach().to(torch.float64).contiguous()
+            gB = cox_nll_backward(ctx.X, ctx.time, ctx.status, g, ctx.ncols, ctx.ws)
+            return gB, None, None, None
+
+    return CoxNLL
+
+
+_COX_NLL = None
+
+
+def cox_nll(B, X, time, status):
+    """Differentiable Cox NLL per column of B (autograd; see CoxNLL)."""
+    global _COX_NLL
+    if _COX_NLL is None:
+        _COX_NLL = _cox_nll_function()
+    return _COX_NLL.apply(B, X, time, status)

@@ -13,19 +13,7 @@
 #include "internal.h"
 #include "survgpu.h"
 
-struct surv_workspace {
-  struct Buf {
-    void* p = nullptr;
-    size_t cap = 0;
-  };
-  enum Id {
-    TIME, STATUS, COLPTR, ROWIDX, VALUES, XD, E, ETA, W2, GEND, DK, CK, GK, GKFF, WK0, WOFF, DTX, BETA, WIDTH, PEN, REC,
-    SLOTS, CTRL, BLOCKCNT, SORTWORK, PERM, PF, WT, AGG, NBUF
-  };
-  int device = -1;
-  Buf bufs[NBUF];
-  survgpu::GraphCache graph;  // instantiated sweep graph of the last fit
-};
+#include "workspace.h"
 
 namespace {
 
@@ -66,7 +54,9 @@ int cuda_code(cudaError_t e) { return e == cudaErrorMemoryAllocation ? SURV_E_NO
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
-int ensure(surv_workspace* ws, int id, size_t bytes, void** out) {
+}  // namespace
+
+int survgpu::ws_ensure(surv_workspace* ws, int id, size_t bytes, void** out) {
   auto& b = ws->bufs[id];
   if (bytes == 0) bytes = 256;
   if (b.cap < bytes) {
@@ -92,8 +82,13 @@ int ensure(surv_workspace* ws, int id, size_t bytes, void** out) {
   return SURV_OK;
 }
 
+namespace {
+
+int ensure(surv_workspace* ws, int id, size_t bytes, void** out) { return survgpu::ws_ensure(ws, id, bytes, out); }
+
 void free_all(surv_workspace* ws) {
   survgpu::graph_cache_free(&ws->graph);
+  survgpu::ws_release_blas(ws);
   for (auto& b : ws->bufs) {
     if (b.p) cudaFree(b.p);
     b.p = nullptr;

@@ -1,0 +1,487 @@
+// Differentiable form (Section 2.9): the Cox negative log partial likelihood
+// (Breslow ties) of C linear predictors at once, eta = X B, and its gradient
+// with respect to B.
+//
+//   forward   Bcat = [B_hi | B_lo] (bf16 split of the FP32 B), one tensor-
+//             core GEMM Y = X Bcat (bf16 x bf16 -> FP32, cuBLAS), then the
+//             risk-set scan: eta = Y_hi + Y_lo, e = exp(eta); every lane of
+//             a warp owns two of the C columns and walks the warp's rows in
+//             order with float-float running sums, so a group end costs its
+//             lanes a store, not a reduction; a per-column kernel adds the
+//             prefix of the warps before, takes d_k log den_k in FP64 and
+//             returns NLL_b = -sum_i delta_i eta_ib + sum_k d_k log den_kb.
+//   backward  Lambda_kb = sum_{k' >= k} d_k' / den_k'b (reverse scan per
+//             column), G_ib = g_b (e_ib Lambda_b(group of i) - delta_i) split
+//             into bf16 [G_hi | G_lo], one GEMM X^T Gcat, halves summed.
+//
+// The GEMMs are plain products and go to cuBLAS; every other step is here.
+#include <cublas_v2.h>
+#include <cuda_bf16.h>
+
+#include <cfloat>
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "common.cuh"
+#include "survgpu.h"
+#include "workspace.h"
+
+namespace survgpu {
+namespace {
+
+constexpr int kNllThreads = 512;   // scan kernels: 16 warps
+constexpr int kNllMaxCols = 64;    // two columns per lane
+constexpr int kRowsAhead = 4;      // rows whose loads a warp keeps in flight
+
+// B (p x C, row-major FP32) -> Bcat (p x 2C, row-major bf16) = [hi | lo]
+__global__ void k_split_b(const float* B, int64_t p, int C, __nv_bfloat16* Bcat) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= p * C) return;
+  const int64_t j = i / C;
+  const int c = (int)(i % C);
+  const float b = B[i];
+  const __nv_bfloat16 hi = __float2bfloat16_rn(b);
+  const __nv_bfloat16 lo = __float2bfloat16_rn(b - __bfloat162float(hi));
+  Bcat[j * 2 * C + c] = hi;
+  Bcat[j * 2 * C + C + c] = lo;
+}
+
+// gBcat (p x 2C, column-major FP32) -> grad_B (p x C, row-major FP32)
+__global__ void k_sum_halves(const float* gBcat, int64_t p, int C, float* grad_B) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= p * C) return;
+  const int64_t j = i / C;
+  const int c = (int)(i % C);
+  grad_B[i] = gBcat[(int64_t)c * p + j] + gBcat[(int64_t)(C + c) * p + j];
+}
+
+// Forward scan.  Warp gw owns rows [gw * rpw, (gw + 1) * rpw); lane l owns
+// columns l and l + 32.  Outputs: rec[k][c] (warp-relative prefix of e at
+// group end k, float-float), wt[gw][c] and wd[gw][c] (the warp's sums of e
+// and of delta * eta).
+__global__ void __launch_bounds__(kNllThreads) k_nll_scan(const float* Y, int64_t n, int C, const int8_t* status,
+                                                          const int32_t* gend, const int32_t* wk0, int64_t rpw,
+                                                          float2* rec, float2* wt, float2* wd) {
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * (kNllThreads / 32) + (threadIdx.x >> 5);
+  const int64_t r_lo = min((int64_t)gw * rpw, n), r_hi = min(r_lo + rpw, n);
+  const int C2 = 2 * C;
+  const bool has0 = lane < C, has1 = lane + 32 < C;
+  ff acc0 = ff_zero(), acc1 = ff_zero(), dl0 = ff_zero(), dl1 = ff_zero();
+  int kn = wk0[gw];
+  const int k_hi = wk0[gw + 1];
+  int64_t next_end = kn < k_hi ? (int64_t)gend[kn] : LLONG_MAX;
+  for (int64_t r0 = r_lo; r0 < r_hi; r0 += kRowsAhead) {
+    float v0[kRowsAhead], v1[kRowsAhead];
+    int8_t st[kRowsAhead];
+#pragma unroll
+    for (int u = 0; u < kRowsAhead; ++u) {
+      const int64_t r = r0 + u;
+      const bool in = r < r_hi;
+      const float* y = Y + r * C2;
+      v0[u] = (in && has0) ? __ldcs(y + lane) + __ldcs(y + C + lane) : 0.f;
+      v1[u] = (in && has1) ? __ldcs(y + 32 + lane) + __ldcs(y + C + 32 + lane) : 0.f;
+      st[u] = in ? status[r] : (int8_t)0;
+    }
+    float p0 = 0.f, p1 = 0.f, q0 = 0.f, q1 = 0.f;
+#pragma unroll
+    for (int u = 0; u < kRowsAhead; ++u) {
+      const int64_t r = r0 + u;
+      const float e0 = has0 ? expf(v0[u]) : 0.f, e1 = has1 ? expf(v1[u]) : 0.f;
+      p0 += e0;
+      p1 += e1;
+      if (st[u] == 1) {
+        q0 += v0[u];
+        q1 += v1[u];
+      }
+      if (r == next_end) {  // a group end: the lane's running prefix is the warp's
+        const ff a0 = ff_add_f(acc0, p0), a1 = ff_add_f(acc1, p1);
+        if (has0) rec[(size_t)kn * C + lane] = make_float2(a0.hi, a0.lo);
+        if (has1) rec[(size_t)kn * C + 32 + lane] = make_float2(a1.hi, a1.lo);
+        ++kn;
+        next_end = kn < k_hi ? (int64_t)gend[kn] : LLONG_MAX;
+      }
+    }
+    acc0 = ff_add_f(acc0, p0);
+    acc1 = ff_add_f(acc1, p1);
+    dl0 = ff_add_f(dl0, q0);
+    dl1 = ff_add_f(dl1, q1);
+  }
+  if (has0) {
+    wt[(size_t)gw * C + lane] = make_float2(acc0.hi, acc0.lo);
+    wd[(size_t)gw * C + lane] = make_float2(dl0.hi, dl0.lo);
+  }
+  if (has1) {
+    wt[(size_t)gw * C + 32 + lane] = make_float2(acc1.hi, acc1.lo);
+    wd[(size_t)gw * C + 32 + lane] = make_float2(dl1.hi, dl1.lo);
+  }
+}
+
+// Per column c (one CTA each): prefix of the warp totals in a fixed order,
+// den_k = prefix before the end's warp + rec[k][c] (kept for the backward),
+// NLL_c = -sum delta eta + sum_k d_k log den_k (logs and the sums in FP64).
+__global__ void __launch_bounds__(256) k_nll_finish(const float2* rec, const float2* wt, const float2* wd, int nwarps,
+                                                   int C, const int32_t* gend, const int32_t* dk, int K, int64_t rpw,
+                                                   double* den, double* nll) {
+  extern __shared__ float2 s_base[];  // [nwarps] exclusive prefix (float-float)
+  __shared__ ff s_chunk[256];
+  __shared__ double s_red[8][2];
+  const int c = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  // 1. chunk sums (thread t: warps [t*ch, (t+1)*ch)), then an exclusive scan
+  //    of the 256 chunk sums by one warp, then the prefix inside each chunk
+  const int ch = (nwarps + 255) / 256;
+  const int w0 = min(tid * ch, nwarps), w1 = min(w0 + ch, nwarps);
+  ff cs = ff_zero();
+  for (int q = w0; q < w1; ++q) {
+    const float2 v = wt[(size_t)q * C + c];
+    cs = ff_add(cs, ff{v.x, v.y});
+  }
+  s_chunk[tid] = cs;
+  __syncthreads();
+  if (w == 0) {
+    ff run = ff_zero();
+    for (int q0 = 0; q0 < 256; q0 += 32) {
+      ff v = s_chunk[q0 + lane];
+      ff incl = warp_inclusive_scan(v, lane);
+      ff ex = shfl_up(incl, 1);
+      if (lane == 0) ex = ff_zero();
+      const ff tot = shfl_idx(incl, 31);
+      s_chunk[q0 + lane] = ff_add(run, ex);
+      run = ff_add(run, tot);
+    }
+  }
+  __syncthreads();
+  ff pre = s_chunk[tid];
+  for (int q = w0; q < w1; ++q) {
+    s_base[q] = make_float2(pre.hi, pre.lo);
+    const float2 v = wt[(size_t)q * C + c];
+    pre = ff_add(pre, ff{v.x, v.y});
+  }
+  __syncthreads();
+  // 2. the group ends: den in FP64, d log den
+  double sl = 0.0, sd = 0.0;
+  for (int k = tid; k < K; k += 256) {
+    const int q = (int)(gend[k] / rpw);
+    const float2 b = s_base[q];
+    const float2 r = rec[(size_t)k * C + c];
+    const ff pk = ff_add(ff{b.x, b.y}, ff{r.x, r.y});
+    const double d = ff_to_d(pk);
+    den[(size_t)k * C + c] = d;
+    if (dk[k] != 0) sl += (double)dk[k] * log(d);
+  }
+  for (int q = tid; q < nwarps; q += 256) {
+    const float2 v = wd[(size_t)q * C + c];
+    sd += (double)v.x + (double)v.y;
+  }
+  sl = warp_sum(sl);
+  sd = warp_sum(sd);
+  if (lane == 0) {
+    s_red[w][0] = sl;
+    s_red[w][1] = sd;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double a = 0.0, b = 0.0;
+    for (int q = 0; q < 8; ++q) {
+      a += s_red[q][0];
+      b += s_red[q][1];
+    }
+    nll[c] = a - b;
+  }
+}
+
+// Backward, per column c (one CTA each): Lambda_k = sum_{k' >= k} d_k' / den_k'
+// (FP64, chunked reverse scan in a fixed order), stored as FP32.
+__global__ void __launch_bounds__(256) k_nll_lambda(const double* den, const int32_t* dk, int K, int C, float* lam) {
+  __shared__ double s_chunk[256];
+  const int c = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int ch = (K + 255) / 256;
+  const int k0 = min(tid * ch, K), k1 = min(k0 + ch, K);
+  double cs = 0.0;
+  for (int k = k0; k < k1; ++k) cs += (double)dk[k] / den[(size_t)k * C + c];
+  s_chunk[tid] = cs;
+  __syncthreads();
+  if (tid == 0) {  // suffix sums of the chunk totals (256 adds)
+    double run = 0.0;
+    for (int q = 255; q >= 0; --q) {
+      const double v = s_chunk[q];
+      s_chunk[q] = run;  // sum of the chunks after q
+      run += v;
+    }
+  }
+  __syncthreads();
+  double run = s_chunk[tid];
+  for (int k = k1 - 1; k >= k0; --k) {
+    run += (double)dk[k] / den[(size_t)k * C + c];
+    lam[(size_t)k * C + c] = (float)run;
+  }
+}
+
+// Backward per row: G_ic = g_c (e_ic Lambda_c(group of i) - delta_i), written
+// as bf16 [hi | lo] (row i: 2C values).
+__global__ void __launch_bounds__(kNllThreads) k_nll_grad(const float* Y, int64_t n, int C, const int8_t* status,
+                                                          const int32_t* gend, const int32_t* wk0, int64_t rpw,
+                                                          const float* lam, const double* gout, __nv_bfloat16* Gcat) {
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * (kNllThreads / 32) + (threadIdx.x >> 5);
+  const int64_t r_lo = min((int64_t)gw * rpw, n), r_hi = min(r_lo + rpw, n);
+  const int C2 = 2 * C;
+  const bool has0 = lane < C, has1 = lane + 32 < C;
+  const float g0 = has0 ? (float)gout[lane] : 0.f, g1 = has1 ? (float)gout[lane + 32] : 0.f;
+  if (r_lo >= r_hi) return;  // warps past the last row
+  int kn = wk0[gw];  // group of the current row: the first end at or after it
+  float l0 = 0.f, l1 = 0.f;
+  auto load_lam = [&]() {
+    l0 = has0 ? lam[(size_t)kn * C + lane] : 0.f;
+    l1 = has1 ? lam[(size_t)kn * C + 32 + lane] : 0.f;
+  };
+  int64_t cur_end = (int64_t)gend[kn];  // every row < n lies in some group (the last row ends one)
+  load_lam();
+  for (int64_t r0 = r_lo; r0 < r_hi; r0 += kRowsAhead) {
+    float v0[kRowsAhead], v1[kRowsAhead];
+    int8_t st[kRowsAhead];
+#pragma unroll
+    for (int u = 0; u < kRowsAhead; ++u) {
+      const int64_t r = r0 + u;
+      const bool in = r < r_hi;
+      const float* y = Y + r * C2;
+      v0[u] = (in && has0) ? __ldcs(y + lane) + __ldcs(y + C + lane) : 0.f;
+      v1[u] = (in && has1) ? __ldcs(y + 32 + lane) + __ldcs(y + C + 32 + lane) : 0.f;
+      st[u] = in ? status[r] : (int8_t)0;
+    }
+#pragma unroll
+    for (int u = 0; u < kRowsAhead; ++u) {
+      const int64_t r = r0 + u;
+      if (r >= r_hi) break;
+      if (r > cur_end) {  // past the end of the current group
+        ++kn;
+        cur_end = (int64_t)gend[kn];
+        load_lam();
+      }
+      const float d = st[u] == 1 ? 1.f : 0.f;
+      __nv_bfloat16* g = Gcat + r * C2;
+      if (has0) {
+        const float x = g0 * (expf(v0[u]) * l0 - d);
+        const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+        g[lane] = hi;
+        g[C + lane] = __float2bfloat16_rn(x - __bfloat162float(hi));
+      }
+      if (has1) {
+        const float x = g1 * (expf(v1[u]) * l1 - d);
+        const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+        g[32 + lane] = hi;
+        g[C + 32 + lane] = __float2bfloat16_rn(x - __bfloat162float(hi));
+      }
+    }
+  }
+}
+
+int cuda_err(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return SURV_OK;
+  char buf[256];
+  snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
+  set_last_error_text(buf);
+  return e == cudaErrorMemoryAllocation ? SURV_E_NOMEM : SURV_E_CUDA;
+}
+
+int blas_err(cublasStatus_t e, const char* what) {
+  if (e == CUBLAS_STATUS_SUCCESS) return SURV_OK;
+  char buf[256];
+  snprintf(buf, sizeof(buf), "%s: cuBLAS status %d", what, (int)e);
+  set_last_error_text(buf);
+  return e == CUBLAS_STATUS_ALLOC_FAILED ? SURV_E_NOMEM : SURV_E_CUDA;
+}
+
+bool on_device(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int get_blas(surv_workspace* ws, cudaStream_t s, cublasHandle_t* h) {
+  if (!ws->blas) {
+    cublasHandle_t nh = nullptr;
+    int rc = blas_err(cublasCreate(&nh), "cublasCreate");
+    if (rc) return rc;
+    ws->blas = nh;
+  }
+  *h = static_cast<cublasHandle_t>(ws->blas);
+  return blas_err(cublasSetStream(*h, s), "cublasSetStream");
+}
+
+struct NllCtrl {
+  unsigned perr;
+  int32_t K;
+  int32_t total_events;
+  int32_t pad;
+};
+
+#define NLL_TRY(expr)        \
+  do {                       \
+    const int rc_ = (expr);  \
+    if (rc_) return rc_;     \
+  } while (0)
+
+}  // namespace
+
+void ws_release_blas(surv_workspace* ws) {
+  if (ws && ws->blas) {
+    cublasDestroy(static_cast<cublasHandle_t>(ws->blas));
+    ws->blas = nullptr;
+  }
+}
+
+}  // namespace survgpu
+
+using survgpu::NllCtrl;
+
+extern "C" {
+
+int cox_nll_forward(const surv_nll_data* d, const float* B, double* nll, void* stream, surv_workspace* ws) {
+  using namespace survgpu;
+  set_last_error_text("");
+  if (!d || !B || !nll || !ws) { set_last_error_text("null argument"); return SURV_E_INVALID; }
+  const int64_t n = d->n, p = d->p;
+  const int C = d->ncols;
+  if (n < 1 || n > 0x7fffffff || p < 1 || p > 0x7fffffff || C < 1 || C > kNllMaxCols) {
+    set_last_error_text("bad sizes (need n >= 1, p >= 1, 1 <= ncols <= 64)");
+    return SURV_E_INVALID;
+  }
+  if (!on_device(d->time) || !on_device(d->status) || !on_device(d->X) || !on_device(B) || !on_device(nll)) {
+    set_last_error_text("time, status, X, B and nll must be device memory");
+    return SURV_E_INVALID;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  using W = surv_workspace;
+  void *ctrl_v, *blk, *gend, *dk, *ck, *wk0, *Y, *Bcat, *rec, *wt, *den;
+  NLL_TRY(ws_ensure(ws, W::NLL_CTRL, sizeof(NllCtrl), &ctrl_v));
+  NllCtrl* ctrl = static_cast<NllCtrl*>(ctrl_v);
+  NLL_TRY(cuda_err(cudaMemsetAsync(ctrl, 0, sizeof(NllCtrl), s), "memset"));
+  const int32_t* time = static_cast<const int32_t*>(d->time);
+  const int8_t* status = static_cast<const int8_t*>(d->status);
+  NLL_TRY(cuda_err(prep_check_times(time, status, n, 0, &ctrl->perr, s), "check times"));
+  const int64_t nb = prep_end_blocks(n);
+  NLL_TRY(ws_ensure(ws, W::NLL_BLK, 4 * (size_t)nb, &blk));
+  NLL_TRY(cuda_err(prep_count_ends(time, n, static_cast<int32_t*>(blk), &ctrl->K, s), "count ends"));
+  NllCtrl hc;
+  NLL_TRY(cuda_err(cudaMemcpyAsync(&hc, ctrl, sizeof(hc), cudaMemcpyDeviceToHost, s), "copy"));
+  NLL_TRY(cuda_err(cudaStreamSynchronize(s), "sync"));
+  if (hc.perr & PREP_UNSORTED) { set_last_error_text("time is not non-increasing"); return SURV_E_UNSORTED; }
+  if (hc.perr & PREP_STATUS) { set_last_error_text("status code out of range"); return SURV_E_STATUS; }
+  const int K = hc.K;
+  NLL_TRY(ws_ensure(ws, W::NLL_GEND, 4 * (size_t)K, &gend));
+  NLL_TRY(ws_ensure(ws, W::NLL_DK, 4 * (size_t)K, &dk));
+  NLL_TRY(ws_ensure(ws, W::GK, 4 * (size_t)K, &ck));
+  NLL_TRY(cuda_err(prep_write_ends(time, n, static_cast<const int32_t*>(blk), static_cast<int32_t*>(gend), s),
+                   "write ends"));
+  NLL_TRY(cuda_err(prep_group_stats(static_cast<int32_t*>(gend), K, status, static_cast<int32_t*>(dk),
+                                    static_cast<int32_t*>(ck), &ctrl->total_events, s),
+                   "group stats"));
+  // row partition of the scan kernels: 2 CTAs of 16 warps per SM
+  int dev = 0, sms = 0;
+  NLL_TRY(cuda_err(cudaGetDevice(&dev), "device"));
+  NLL_TRY(cuda_err(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count"));
+  const int G = 2 * sms, wpc = kNllThreads / 32, nwarps = G * wpc;
+  const int64_t nwords = (n + 31) / 32;
+  const int64_t wpw = (nwords + nwarps - 1) / nwarps;
+  const int64_t rpw = wpw * 32;
+  NLL_TRY(ws_ensure(ws, W::NLL_WK0, 4 * (size_t)(nwarps + 1), &wk0));
+  NLL_TRY(cuda_err(prep_warp_groups(static_cast<int32_t*>(gend), K, n, nwarps, rpw, static_cast<int32_t*>(wk0), s),
+                   "warp groups"));
+  // Y = X [B_hi | B_lo]
+  NLL_TRY(ws_ensure(ws, W::NLL_Y, sizeof(float) * (size_t)n * 2 * C, &Y));
+  NLL_TRY(ws_ensure(ws, W::NLL_BCAT, sizeof(__nv_bfloat16) * (size_t)p * 2 * C, &Bcat));
+  const int64_t pc = p * C;
+  k_split_b<<<(unsigned)((pc + 255) / 256), 256, 0, s>>>(B, p, C, static_cast<__nv_bfloat16*>(Bcat));
+  NLL_TRY(cuda_err(cudaGetLastError(), "split B"));
+  cublasHandle_t h;
+  NLL_TRY(get_blas(ws, s, &h));
+  const float one = 1.f, zero = 0.f;
+  // column-major view: Y^T (2C x n) = Bcat^T (2C x p) * X^T (p x n)
+  NLL_TRY(blas_err(cublasGemmEx(h, CUBLAS_OP_N, CUBLAS_OP_N, 2 * C, (int)n, (int)p, &one, Bcat, CUDA_R_16BF, 2 * C,
+                                d->X, CUDA_R_16BF, (int)p, &zero, Y, CUDA_R_32F, 2 * C, CUBLAS_COMPUTE_32F,
+                                CUBLAS_GEMM_DEFAULT),
+                   "GEMM X B"));
+  NLL_TRY(ws_ensure(ws, W::NLL_REC, sizeof(float2) * (size_t)K * C, &rec));
+  NLL_TRY(ws_ensure(ws, W::NLL_WT, 2 * sizeof(float2) * (size_t)nwarps * C, &wt));
+  NLL_TRY(ws_ensure(ws, W::NLL_DEN, sizeof(double) * (size_t)K * C, &den));
+  float2* wt2 = static_cast<float2*>(wt);
+  k_nll_scan<<<G, kNllThreads, 0, s>>>(static_cast<const float*>(Y), n, C, status, static_cast<int32_t*>(gend),
+                                       static_cast<int32_t*>(wk0), rpw, static_cast<float2*>(rec), wt2,
+                                       wt2 + (size_t)nwarps * C);
+  NLL_TRY(cuda_err(cudaGetLastError(), "scan"));
+  const size_t smem = sizeof(float2) * (size_t)nwarps;
+  if (smem > 48 * 1024)
+    NLL_TRY(cuda_err(cudaFuncSetAttribute(k_nll_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                     "smem"));
+  k_nll_finish<<<C, 256, smem, s>>>(static_cast<float2*>(rec), wt2, wt2 + (size_t)nwarps * C, nwarps, C,
+                                    static_cast<int32_t*>(gend), static_cast<int32_t*>(dk), K, rpw,
+                                    static_cast<double*>(den), nll);
+  NLL_TRY(cuda_err(cudaGetLastError(), "finish"));
+  ws->nll_n = n;
+  ws->nll_p = (int32_t)p;
+  ws->nll_c = C;
+  ws->nll_K = K;
+  ws->nll_G = G;
+  ws->nll_wpc = wpc;
+  ws->nll_wpw = (int32_t)wpw;
+  ws->nll_x = d->X;
+  return SURV_OK;
+}
+
+int cox_nll_backward(const surv_nll_data* d, const double* grad_nll, float* grad_B, void* stream,
+                     surv_workspace* ws) {
+  using namespace survgpu;
+  set_last_error_text("");
+  if (!d || !grad_nll || !grad_B || !ws) { set_last_error_text("null argument"); return SURV_E_INVALID; }
+  if (ws->nll_n != d->n || ws->nll_p != d->p || ws->nll_c != d->ncols || ws->nll_x != d->X) {
+    set_last_error_text("cox_nll_backward must follow cox_nll_forward on the same data and workspace");
+    return SURV_E_INVALID;
+  }
+  if (!on_device(grad_nll) || !on_device(grad_B)) {
+    set_last_error_text("grad_nll and grad_B must be device memory");
+    return SURV_E_INVALID;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  using W = surv_workspace;
+  const int64_t n = d->n, p = d->p;
+  const int C = d->ncols, K = ws->nll_K, G = ws->nll_G, nwarps = G * ws->nll_wpc;
+  const int64_t rpw = (int64_t)ws->nll_wpw * 32;
+  void *lam, *G2, *gB;
+  NLL_TRY(ws_ensure(ws, W::NLL_LAM, sizeof(float) * (size_t)K * C, &lam));
+  NLL_TRY(ws_ensure(ws, W::NLL_G, sizeof(__nv_bfloat16) * (size_t)n * 2 * C, &G2));
+  NLL_TRY(ws_ensure(ws, W::NLL_GB, sizeof(float) * (size_t)p * 2 * C, &gB));
+  const double* den = static_cast<const double*>(ws->bufs[W::NLL_DEN].p);
+  const int32_t* dk = static_cast<const int32_t*>(ws->bufs[W::NLL_DK].p);
+  const int32_t* gend = static_cast<const int32_t*>(ws->bufs[W::NLL_GEND].p);
+  const int32_t* wk0 = static_cast<const int32_t*>(ws->bufs[W::NLL_WK0].p);
+  k_nll_lambda<<<C, 256, 0, s>>>(den, dk, K, C, static_cast<float*>(lam));
+  NLL_TRY(cuda_err(cudaGetLastError(), "lambda"));
+  k_nll_grad<<<G, kNllThreads, 0, s>>>(static_cast<const float*>(ws->bufs[W::NLL_Y].p), n, C,
+                                       static_cast<const int8_t*>(d->status), gend, wk0, rpw,
+                                       static_cast<float*>(lam), grad_nll, static_cast<__nv_bfloat16*>(G2));
+  NLL_TRY(cuda_err(cudaGetLastError(), "grad"));
+  (void)nwarps;
+  cublasHandle_t h;
+  NLL_TRY(get_blas(ws, s, &h));
+  const float one = 1.f, zero = 0.f;
+  // column-major: gBcat (p x 2C) = X^T (p x n) * Gcat (n x 2C); Gcat is stored
+  // row-major n x 2C, i.e. column-major (2C x n), hence the transpose
+  NLL_TRY(blas_err(cublasGemmEx(h, CUBLAS_OP_N, CUBLAS_OP_T, (int)p, 2 * C, (int)n, &one, d->X, CUDA_R_16BF, (int)p,
+                                G2, CUDA_R_16BF, 2 * C, &zero, gB, CUDA_R_32F, (int)p, CUBLAS_COMPUTE_32F,
+                                CUBLAS_GEMM_DEFAULT),
+                   "GEMM X^T G"));
+  const int64_t pc = p * C;
+  k_sum_halves<<<(unsigned)((pc + 255) / 256), 256, 0, s>>>(static_cast<const float*>(gB), p, C, grad_B);
+  return cuda_err(cudaGetLastError(), "sum halves");
+}
+
+}  // extern "C"

@@ -1,0 +1,40 @@
+// The opaque surv_workspace of the C ABI: device buffers that grow on demand
+// and are reused across calls, the cached sweep graph of the last fit, and
+// the state the differentiable form keeps between its forward and backward
+// calls.  Internal to the library.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include "internal.h"
+
+struct surv_workspace {
+  struct Buf {
+    void* p = nullptr;
+    size_t cap = 0;
+  };
+  enum Id {
+    TIME, STATUS, COLPTR, ROWIDX, VALUES, XD, E, ETA, W2, GEND, DK, CK, GK, GKFF, WK0, WOFF, DTX, BETA, WIDTH, PEN, REC,
+    SLOTS, CTRL, BLOCKCNT, SORTWORK, PERM, PF, WT, AGG,
+    // differentiable form (cox_nll_forward / cox_nll_backward)
+    NLL_Y, NLL_BCAT, NLL_REC, NLL_WT, NLL_DEN, NLL_LAM, NLL_G, NLL_GB, NLL_GEND, NLL_DK, NLL_WK0, NLL_BLK,
+    NLL_CTRL,
+    NBUF
+  };
+  int device = -1;
+  Buf bufs[NBUF];
+  survgpu::GraphCache graph;  // instantiated sweep graph of the last fit
+  void* blas = nullptr;       // cublasHandle_t, created on first use
+  // shape of the last cox_nll_forward (what cox_nll_backward continues from)
+  int64_t nll_n = -1;
+  int32_t nll_p = 0, nll_c = 0, nll_K = 0, nll_G = 0, nll_wpc = 0, nll_wpw = 0;
+  const void* nll_x = nullptr;
+};
+
+namespace survgpu {
+// Grow buffer `id` to at least `bytes` (api.cu); SURV_* error code.
+int ws_ensure(surv_workspace* ws, int id, size_t bytes, void** out);
+// Destroy the cuBLAS handle of a workspace, if any (nll.cu).
+void ws_release_blas(surv_workspace* ws);
+}  // namespace survgpu

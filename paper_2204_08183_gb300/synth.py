@@ -36,6 +36,7 @@ __all__ = [
     "cohort_fg_dense",
     "cohort_small",
     "csc_from_dense",
+    "nll_cohort",
 ]
 
 
@@ -232,3 +233,16 @@ def cohort_small(n, p, seed, n_times=None, censor_frac=0.3, competing_frac=0.0,
         "beta": beta,
         "layout": "dense",
     }
+
+
+def nll_cohort(n, p, C, seed, n_times=5000, censor_frac=0.3, b_sd=0.05):
+    """Inputs of the differentiable form: X ~ N(0, 1) float32 (n, p)
+    row-major (the caller rounds it to bfloat16), B ~ N(0, b_sd^2) float32
+    (p, C), integer times uniform on 1..n_times in decreasing order, status
+    1 (event) with probability 1 - censor_frac, else 0."""
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((n, p), dtype=np.float32)
+    B = rng.normal(0.0, b_sd, size=(p, C)).astype(np.float32)
+    time = np.sort(rng.integers(1, n_times + 1, size=n).astype(np.int32))[::-1].copy()
+    status = (rng.random(n) >= censor_frac).astype(np.int8)
+    return {"X": X, "B": B, "time": time, "status": status}

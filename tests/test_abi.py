@@ -57,6 +57,9 @@ int main(void) {
   printf("surv_data %zu\n", sizeof(surv_data));
   printf("surv_opts %zu\n", sizeof(surv_opts));
   printf("surv_fit_info %zu\n", sizeof(surv_fit_info));
+  printf("surv_nll_data %zu\n", sizeof(surv_nll_data));
+  F(surv_nll_data, n); F(surv_nll_data, p); F(surv_nll_data, ncols); F(surv_nll_data, time);
+  F(surv_nll_data, status); F(surv_nll_data, X);
   F(surv_data, n); F(surv_data, p); F(surv_data, time); F(surv_data, status); F(surv_data, layout);
   F(surv_data, dtype); F(surv_data, col_ptr); F(surv_data, row_idx); F(surv_data, values);
   F(surv_opts, penalty); F(surv_opts, precision); F(surv_opts, lambda); F(surv_opts, penalty_factor);
@@ -74,7 +77,7 @@ int main(void) {
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
     c = dict(line.split() for line in out if line.strip())
     structs = {"surv_data": binding.surv_data, "surv_opts": binding.surv_opts,
-               "surv_fit_info": binding.surv_fit_info}
+               "surv_fit_info": binding.surv_fit_info, "surv_nll_data": binding.surv_nll_data}
     for name, cls in structs.items():
         assert int(c[name]) == C.sizeof(cls), name
     for key, off in c.items():
