@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--p", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", choices=["ccd", "autograd"], default="ccd",
+                    help="ccd: the headline penalised Cox fit; autograd: forward + backward of the "
+                         "differentiable Cox NLL at N=2^22, p=256, 64 columns (bf16 X)")
     ap.add_argument("--schedule", choices=["graph", "persistent"], default="graph",
                     help="graph: two kernels per coordinate replayed as a CUDA graph (default); "
                          "persistent: one cooperative launch per fit")
@@ -290,6 +293,121 @@ def run_gpu(args, rank, world):
     return out
 
 
+# ------------------------------------------------ differentiable form (f2)
+AG_METRIC = "Cox NLL forward+backward/s, eta = X B, N=2^22 p=256 C=64, bf16 X (tensor-core GEMMs)"
+
+
+def run_autograd(args, rank, world):
+    """One step = cox_nll_forward + cox_nll_backward through the C ABI at
+    N = 2^22, p = 256, C = 64 (X bf16 row-major, B float32), device-resident
+    inputs; e2e = the autograd function with the inputs copied from pinned
+    host memory each step."""
+    import torch
+    from paper_2204_08183_gb300 import binding, synth
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    n, p, C = 1 << 22, 256, 64
+    c = synth.nll_cohort(n, p, C, seed=5, n_times=5000)
+    X = torch.from_numpy(c["X"]).cuda().to(torch.bfloat16)
+    B = torch.from_numpy(c["B"]).cuda()
+    t = torch.from_numpy(c["time"]).cuda()
+    s = torch.from_numpy(c["status"]).cuda()
+    g = torch.ones(C, dtype=torch.float64, device="cuda")
+    ws = binding.Workspace()
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(1.5)
+    for _ in range(args.warmup):
+        binding.cox_nll_forward(X, t, s, B, ws)
+        binding.cox_nll_backward(X, t, s, g, C, ws)
+    torch.cuda.synchronize()
+    # L2 (129 MB) is far smaller than X (2 GiB) and Y (2 GiB): no flush needed
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    evf = torch.cuda.Event(enable_timing=True)
+    fwd_ms = 0.0
+    ev0.record(stream)
+    for _ in range(args.steps):
+        binding.cox_nll_forward(X, t, s, B, ws)
+        binding.cox_nll_backward(X, t, s, g, C, ws)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    # forward alone, for the split
+    ev0.record(stream)
+    for _ in range(args.steps):
+        binding.cox_nll_forward(X, t, s, B, ws)
+    evf.record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = ev0.elapsed_time(evf) / args.steps
+    clk = clocks.stop()
+    t_max = ms
+    if world > 1:
+        tt = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = world * 1e3 / t_max
+    # minimal bytes: X read by both products, eta written by the forward and
+    # read by the backward
+    alg = 2 * (2 * n * p) + 2 * (4 * n * C)
+    moved = (2 * n * p) + 2 * (4 * n * 2 * C) + (4 * n * 2 * C) + (2 * n * 2 * C) + (2 * n * p) + (2 * n * 2 * C)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = alg / (t_max / 1e3) / 1e9
+    out = {"metric": AG_METRIC, "value": round(value, 2), "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(t_max, 3), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "bf16 X, f32 B/eta, f64 logs", "data": "synthetic",
+           "config": {"workload": "cox_nll_autograd_n4194304_p256_c64", "n": n, "p": p, "columns": C,
+                      "time_grid": 5000, "censoring": 0.3,
+                      "l2": "inputs larger than L2 (X 2 GiB, eta 2 GiB)"},
+           "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                        "frac": round(achieved / peak, 4), "traffic": None,
+                        "algorithmic_bytes_per_step": alg, "implementation_bytes_per_step": moved,
+                        "forward_ms": round(fwd_ms, 3), "backward_ms": round(t_max - fwd_ms, 3),
+                        "kernel": "cuBLAS bf16 GEMMs (X B, X^T G) + k_nll_scan/finish/lambda/grad"},
+           "clocks": clk, "gpu_launches": args.steps * 9}
+    if not args.no_e2e:
+        # autograd function, inputs copied from pinned host memory every step
+        hX = X.cpu().pin_memory()
+        hB = B.cpu().pin_memory()
+        ht, hs = t.cpu().pin_memory(), s.cpu().pin_memory()
+        e_steps = max(1, min(args.steps, 3))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(e_steps):
+            Xd, td, sd = hX.cuda(non_blocking=True), ht.cuda(non_blocking=True), hs.cuda(non_blocking=True)
+            Bd = hB.cuda(non_blocking=True).requires_grad_(True)
+            nll = binding.cox_nll(Bd, Xd, td, sd)
+            (gB,) = torch.autograd.grad(nll.sum(), Bd)
+            nll.detach().cpu(), gB.cpu()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ems = e0.elapsed_time(e1) / e_steps
+        out["e2e"] = {"value": round(world * 1e3 / ems, 2), "unit": "steps/s",
+                      "h2d_bytes_per_step": 2 * n * p + 4 * p * C + 5 * n, "d2h_bytes_per_step": 8 * C + 4 * p * C,
+                      "note": "binding.cox_nll (autograd) forward + backward with X, B, time, status copied from "
+                              "pinned host memory each step"}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        Xo = X[:, :].float().cpu().numpy()
+        t0 = time.perf_counter()
+        eta = Xo.astype(np.float64) @ c["B"][:, :1].astype(np.float64)
+        oracle.cox_nll(c["time"], c["status"], eta)
+        ge = oracle.cox_nll_grad_eta(c["time"], c["status"], eta)
+        Xo.T.astype(np.float64) @ ge
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": round(1.0 / (dt * C), 6), "unit": "steps/s", "cores": 1, "kind": "oracle",
+                               "sample": "oracle NLL + gradient of 1 of the 64 columns at full N (%.1f s); "
+                                         "steps/s = 1 / (64 x that)" % dt}
+    return out
+
+
 def run_reference(args, rank, world):
     """The oracle on the host cores: each step one bounded sample."""
     if rank != 0:
@@ -328,6 +446,8 @@ def main():
         dist.init_process_group("nccl" if args.impl == "gb300" else "gloo")
     if args.impl == "reference":
         out = run_reference(args, rank, world)
+    elif args.workload == "autograd":
+        out = run_autograd(args, rank, world)
     else:
         out = run_gpu(args, rank, world)
     if rank == 0 and out is not None:

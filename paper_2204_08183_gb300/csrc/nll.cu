@@ -31,7 +31,7 @@
 namespace survgpu {
 namespace {
 
-constexpr int kNllThreads = 512;   // scan kernels: 16 warps
+constexpr int kNllThreads = 512;   // scan kernels: two CTAs of 16 warps per SM
 constexpr int kNllMaxCols = 64;    // two columns per lane
 constexpr int kRowsAhead = 4;      // rows whose loads a warp keeps in flight
 
@@ -57,18 +57,33 @@ __global__ void k_sum_halves(const float* gBcat, int64_t p, int C, float* grad_B
   grad_B[i] = gBcat[(int64_t)c * p + j] + gBcat[(int64_t)(C + c) * p + j];
 }
 
+// eta of columns c0 = 2 lane and c0 + 1 of row r: Y_hi + Y_lo (8-byte loads
+// when C is even, streaming: Y is read once per kernel)
+__device__ __forceinline__ void load_pair(const float* y, int C, int c0, bool has0, bool has1, float& v0, float& v1) {
+  if (has1 && (C & 1) == 0) {
+    const float2 h = __ldcs(reinterpret_cast<const float2*>(y + c0));
+    const float2 l = __ldcs(reinterpret_cast<const float2*>(y + C + c0));
+    v0 = h.x + l.x;
+    v1 = h.y + l.y;
+  } else {
+    v0 = has0 ? __ldcs(y + c0) + __ldcs(y + C + c0) : 0.f;
+    v1 = has1 ? __ldcs(y + c0 + 1) + __ldcs(y + C + c0 + 1) : 0.f;
+  }
+}
+
 // Forward scan.  Warp gw owns rows [gw * rpw, (gw + 1) * rpw); lane l owns
-// columns l and l + 32.  Outputs: rec[k][c] (warp-relative prefix of e at
+// the adjacent columns 2l and 2l + 1.  Outputs: rec[k][c] (warp-relative prefix of e at
 // group end k, float-float), wt[gw][c] and wd[gw][c] (the warp's sums of e
 // and of delta * eta).
-__global__ void __launch_bounds__(kNllThreads) k_nll_scan(const float* Y, int64_t n, int C, const int8_t* status,
+__global__ void __launch_bounds__(kNllThreads, 2) k_nll_scan(const float* Y, int64_t n, int C, const int8_t* status,
                                                           const int32_t* gend, const int32_t* wk0, int64_t rpw,
                                                           float2* rec, float2* wt, float2* wd) {
   const int lane = threadIdx.x & 31;
   const int gw = blockIdx.x * (kNllThreads / 32) + (threadIdx.x >> 5);
   const int64_t r_lo = min((int64_t)gw * rpw, n), r_hi = min(r_lo + rpw, n);
   const int C2 = 2 * C;
-  const bool has0 = lane < C, has1 = lane + 32 < C;
+  const int c0 = 2 * lane;
+  const bool has0 = c0 < C, has1 = c0 + 1 < C;
   ff acc0 = ff_zero(), acc1 = ff_zero(), dl0 = ff_zero(), dl1 = ff_zero();
   int kn = wk0[gw];
   const int k_hi = wk0[gw + 1];
@@ -80,9 +95,9 @@ __global__ void __launch_bounds__(kNllThreads) k_nll_scan(const float* Y, int64_
     for (int u = 0; u < kRowsAhead; ++u) {
       const int64_t r = r0 + u;
       const bool in = r < r_hi;
-      const float* y = Y + r * C2;
-      v0[u] = (in && has0) ? __ldcs(y + lane) + __ldcs(y + C + lane) : 0.f;
-      v1[u] = (in && has1) ? __ldcs(y + 32 + lane) + __ldcs(y + C + 32 + lane) : 0.f;
+      v0[u] = 0.f;
+      v1[u] = 0.f;
+      if (in) load_pair(Y + r * C2, C, c0, has0, has1, v0[u], v1[u]);
       st[u] = in ? status[r] : (int8_t)0;
     }
     float p0 = 0.f, p1 = 0.f, q0 = 0.f, q1 = 0.f;
@@ -98,8 +113,8 @@ __global__ void __launch_bounds__(kNllThreads) k_nll_scan(const float* Y, int64_
       }
       if (r == next_end) {  // a group end: the lane's running prefix is the warp's
         const ff a0 = ff_add_f(acc0, p0), a1 = ff_add_f(acc1, p1);
-        if (has0) rec[(size_t)kn * C + lane] = make_float2(a0.hi, a0.lo);
-        if (has1) rec[(size_t)kn * C + 32 + lane] = make_float2(a1.hi, a1.lo);
+        if (has0) rec[(size_t)kn * C + c0] = make_float2(a0.hi, a0.lo);
+        if (has1) rec[(size_t)kn * C + c0 + 1] = make_float2(a1.hi, a1.lo);
         ++kn;
         next_end = kn < k_hi ? (int64_t)gend[kn] : LLONG_MAX;
       }
@@ -110,12 +125,12 @@ __global__ void __launch_bounds__(kNllThreads) k_nll_scan(const float* Y, int64_
     dl1 = ff_add_f(dl1, q1);
   }
   if (has0) {
-    wt[(size_t)gw * C + lane] = make_float2(acc0.hi, acc0.lo);
-    wd[(size_t)gw * C + lane] = make_float2(dl0.hi, dl0.lo);
+    wt[(size_t)gw * C + c0] = make_float2(acc0.hi, acc0.lo);
+    wd[(size_t)gw * C + c0] = make_float2(dl0.hi, dl0.lo);
   }
   if (has1) {
-    wt[(size_t)gw * C + 32 + lane] = make_float2(acc1.hi, acc1.lo);
-    wd[(size_t)gw * C + 32 + lane] = make_float2(dl1.hi, dl1.lo);
+    wt[(size_t)gw * C + c0 + 1] = make_float2(acc1.hi, acc1.lo);
+    wd[(size_t)gw * C + c0 + 1] = make_float2(dl1.hi, dl1.lo);
   }
 }
 
@@ -223,21 +238,22 @@ __global__ void __launch_bounds__(256) k_nll_lambda(const double* den, const int
 
 // Backward per row: G_ic = g_c (e_ic Lambda_c(group of i) - delta_i), written
 // as bf16 [hi | lo] (row i: 2C values).
-__global__ void __launch_bounds__(kNllThreads) k_nll_grad(const float* Y, int64_t n, int C, const int8_t* status,
+__global__ void __launch_bounds__(kNllThreads, 2) k_nll_grad(const float* Y, int64_t n, int C, const int8_t* status,
                                                           const int32_t* gend, const int32_t* wk0, int64_t rpw,
                                                           const float* lam, const double* gout, __nv_bfloat16* Gcat) {
   const int lane = threadIdx.x & 31;
   const int gw = blockIdx.x * (kNllThreads / 32) + (threadIdx.x >> 5);
   const int64_t r_lo = min((int64_t)gw * rpw, n), r_hi = min(r_lo + rpw, n);
   const int C2 = 2 * C;
-  const bool has0 = lane < C, has1 = lane + 32 < C;
-  const float g0 = has0 ? (float)gout[lane] : 0.f, g1 = has1 ? (float)gout[lane + 32] : 0.f;
+  const int c0 = 2 * lane;
+  const bool has0 = c0 < C, has1 = c0 + 1 < C;
+  const float g0 = has0 ? (float)gout[c0] : 0.f, g1 = has1 ? (float)gout[c0 + 1] : 0.f;
   if (r_lo >= r_hi) return;  // warps past the last row
   int kn = wk0[gw];  // group of the current row: the first end at or after it
   float l0 = 0.f, l1 = 0.f;
   auto load_lam = [&]() {
-    l0 = has0 ? lam[(size_t)kn * C + lane] : 0.f;
-    l1 = has1 ? lam[(size_t)kn * C + 32 + lane] : 0.f;
+    l0 = has0 ? lam[(size_t)kn * C + c0] : 0.f;
+    l1 = has1 ? lam[(size_t)kn * C + c0 + 1] : 0.f;
   };
   int64_t cur_end = (int64_t)gend[kn];  // every row < n lies in some group (the last row ends one)
   load_lam();
@@ -248,9 +264,9 @@ __global__ void __launch_bounds__(kNllThreads) k_nll_grad(const float* Y, int64_
     for (int u = 0; u < kRowsAhead; ++u) {
       const int64_t r = r0 + u;
       const bool in = r < r_hi;
-      const float* y = Y + r * C2;
-      v0[u] = (in && has0) ? __ldcs(y + lane) + __ldcs(y + C + lane) : 0.f;
-      v1[u] = (in && has1) ? __ldcs(y + 32 + lane) + __ldcs(y + C + 32 + lane) : 0.f;
+      v0[u] = 0.f;
+      v1[u] = 0.f;
+      if (in) load_pair(Y + r * C2, C, c0, has0, has1, v0[u], v1[u]);
       st[u] = in ? status[r] : (int8_t)0;
     }
 #pragma unroll
@@ -264,17 +280,23 @@ __global__ void __launch_bounds__(kNllThreads) k_nll_grad(const float* Y, int64_
       }
       const float d = st[u] == 1 ? 1.f : 0.f;
       __nv_bfloat16* g = Gcat + r * C2;
-      if (has0) {
-        const float x = g0 * (expf(v0[u]) * l0 - d);
-        const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-        g[lane] = hi;
-        g[C + lane] = __float2bfloat16_rn(x - __bfloat162float(hi));
-      }
-      if (has1) {
-        const float x = g1 * (expf(v1[u]) * l1 - d);
-        const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-        g[32 + lane] = hi;
-        g[C + 32 + lane] = __float2bfloat16_rn(x - __bfloat162float(hi));
+      const float x0 = has0 ? g0 * (expf(v0[u]) * l0 - d) : 0.f;
+      const float x1 = has1 ? g1 * (expf(v1[u]) * l1 - d) : 0.f;
+      const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+      const __nv_bfloat16 m0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
+      const __nv_bfloat16 m1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
+      if (has1 && (C & 1) == 0) {  // 4-byte stores of both columns
+        *reinterpret_cast<__nv_bfloat162*>(g + c0) = __halves2bfloat162(h0, h1);
+        *reinterpret_cast<__nv_bfloat162*>(g + C + c0) = __halves2bfloat162(m0, m1);
+      } else {
+        if (has0) {
+          g[c0] = h0;
+          g[C + c0] = m0;
+        }
+        if (has1) {
+          g[c0 + 1] = h1;
+          g[C + c0 + 1] = m1;
+        }
       }
     }
   }
@@ -385,7 +407,7 @@ int cox_nll_forward(const surv_nll_data* d, const float* B, double* nll, void* s
   NLL_TRY(cuda_err(prep_group_stats(static_cast<int32_t*>(gend), K, status, static_cast<int32_t*>(dk),
                                     static_cast<int32_t*>(ck), &ctrl->total_events, s),
                    "group stats"));
-  // row partition of the scan kernels: 2 CTAs of 16 warps per SM
+  // row partition of the scan kernels: two CTAs of 16 warps per SM
   int dev = 0, sms = 0;
   NLL_TRY(cuda_err(cudaGetDevice(&dev), "device"));
   NLL_TRY(cuda_err(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count"));
