@@ -246,3 +246,20 @@ def nll_cohort(n, p, C, seed, n_times=5000, censor_frac=0.3, b_sd=0.05):
     time = np.sort(rng.integers(1, n_times + 1, size=n).astype(np.int32))[::-1].copy()
     status = (rng.random(n) >= censor_frac).astype(np.int8)
     return {"X": X, "B": B, "time": time, "status": status}
+
+
+def cv_folds(n, nfolds, seed, lo=0.8, hi=1.2):
+    """Uneven random fold assignment (int8 [n]): fold sizes spaced evenly
+    from lo to hi times n / nfolds (rescaled to sum to n), subjects assigned
+    to folds by a random permutation."""
+    rng = np.random.default_rng(seed)
+    w = np.linspace(lo, hi, nfolds) if nfolds > 1 else np.ones(1)
+    sizes = np.floor(w / w.sum() * n).astype(np.int64)
+    sizes[: n - sizes.sum()] += 1
+    fold = np.repeat(np.arange(nfolds, dtype=np.int8), sizes)
+    return np.ascontiguousarray(fold[rng.permutation(n)])
+
+
+def lambda_grid(lambda_max, nlambda, ratio=1e-3):
+    """nlambda log-spaced strengths from lambda_max down to ratio * lambda_max."""
+    return lambda_max * np.logspace(0.0, np.log10(ratio), nlambda)
