@@ -271,6 +271,64 @@ int cox_nll_forward(const surv_nll_data *data, const float *B, double *nll, void
 int cox_nll_backward(const surv_nll_data *data, const double *grad_nll, float *grad_B, void *stream,
                      surv_workspace *ws);
 
+/* ---- cross-validated penalty path (Section 2.8) ------------------------ */
+
+/* Largest useful L1 strength for Cox: the smallest gamma whose penalised
+ * optimum is beta = 0, i.e. max over penalised j of |l'_j(0)| / pf_j (the
+ * Karush-Kuhn-Tucker condition of Section 2.3 at 0).  At beta = 0 every e_i
+ * is 1, so l'_j(0) = sum_i x_ij (delta_i - Lambda(i)) with Lambda(i) the sum
+ * of d_k / |R_k| over the tie groups whose risk set holds i; the sums run in
+ * FP64 on the device.
+ *   data: as for cox_fit (either layout and dtype).  penalty_factor [p]
+ *   (host or device) or NULL for all ones.  *lambda_max: host double.
+ *   stream: cudaStream_t or NULL.  Errors as cox_fit. */
+int cox_lambda_max(const surv_data *data, const double *penalty_factor, double *lambda_max, void *stream);
+
+typedef struct surv_cv_info {
+  int32_t nfits;                 /* nlambda * nfolds                                 */
+  int32_t best_lambda;           /* index of the largest mean held-out score         */
+  int32_t max_sweeps_used;       /* most sweeps of any fit                           */
+  int32_t fits_converged;        /* fits that met the tolerance                      */
+  int32_t graph_replays;         /* replays of the batched sweep graph               */
+  int32_t ctas_per_fit;          /* CTAs each fit runs on in the batched kernels     */
+  int64_t kernel_launches;       /* CUDA kernels launched (graph nodes counted)      */
+  int64_t n_groups;              /* tie groups K of the whole data                   */
+  double ccd_kernel_ms;          /* batched CCD: first replay to the last stop       */
+  double heldout_ms;             /* held-out scores and the choice of lambda         */
+} surv_cv_info;
+
+/* K-fold cross-validation over a penalty path for Cox (Section 2.8): one
+ * penalised fit per (lambda, fold) pair, F = nlambda * nfolds fits in all,
+ * each on the subjects outside its fold, all run together: every kernel of
+ * the per-coordinate schedule carries every fit (one fit per grid row), the
+ * sweep is captured once as a CUDA graph and replayed until every fit has
+ * stopped by its own rule.  A held-out subject keeps e = 0 in its fit, so
+ * it is in no risk set, and each fold has its own event counts d_k and
+ * delta^T X_j; X and the tie groups are shared.  Every fit starts from
+ * beta = 0 (cold start).
+ *
+ * Afterwards each fit's held-out score is the log partial likelihood of the
+ * subjects of its fold alone, on their own risk sets, at the fit's beta
+ * (Breslow ties as in Eq. cox_l); the path's score at lambda l is the mean
+ * over folds, and best_lambda is the first index with the largest score.
+ *   data: as for cox_fit.  fold_id [n] int8 (host or device), the fold
+ *   0..nfolds-1 of each subject in data order; every fold's training part
+ *   needs an event (SURV_E_NO_EVENTS otherwise).  lambdas [nlambda] host
+ *   doubles >= 0.  opts: penalty (L1 or L2), precision, tol, max_sweeps,
+ *   penalty_factor, stream and workspace as for cox_fit (lambda and flags
+ *   are ignored).  ctas_per_fit: CTAs per fit in the batched kernels, or 0
+ *   to choose it from the device's SM count and the number of fits.
+ * Outputs (host or device, any may be NULL except beta_out):
+ *   beta_out [nlambda][nfolds][p] doubles (fit f = l * nfolds + k),
+ *   heldout [nlambda][nfolds], cv_mean [nlambda] doubles,
+ *   sweeps [nlambda][nfolds] int32, info (host).
+ * Returns SURV_OK when every fit converged, SURV_W_NOT_CONVERGED when some
+ * stopped at max_sweeps (all outputs are written), or an error code.
+ * 1 <= nfolds <= 127, 1 <= nlambda, F <= 65535. */
+int cox_cv_path(const surv_data *data, const int8_t *fold_id, int32_t nfolds, const double *lambdas,
+                int32_t nlambda, const surv_opts *opts, int32_t ctas_per_fit, double *beta_out,
+                double *heldout, double *cv_mean, int32_t *sweeps, surv_cv_info *info);
+
 /* Short name of a return code (static string). */
 const char *surv_strerror(int code);
 

@@ -42,7 +42,8 @@ SURV_FLAG_PERSISTENT = 2
 # exported symbols, in the order the header declares them
 EXPORTS = ["surv_opts_default", "surv_workspace_create", "surv_workspace_destroy", "surv_sort_desc",
            "cox_fit", "fg_fit", "loglik_grad_hess", "surv_groups", "loglik_grad_hess_noalloc",
-           "cox_nll_forward", "cox_nll_backward", "surv_strerror", "surv_last_error", "surv_version"]
+           "cox_nll_forward", "cox_nll_backward", "cox_lambda_max", "cox_cv_path", "surv_strerror",
+           "surv_last_error", "surv_version"]
 
 
 class surv_data(C.Structure):
@@ -76,6 +77,16 @@ class surv_fit_info(C.Structure):
         return d
 
 
+class surv_cv_info(C.Structure):
+    _fields_ = [("nfits", C.c_int32), ("best_lambda", C.c_int32), ("max_sweeps_used", C.c_int32),
+                ("fits_converged", C.c_int32), ("graph_replays", C.c_int32), ("ctas_per_fit", C.c_int32),
+                ("kernel_launches", C.c_int64), ("n_groups", C.c_int64), ("ccd_kernel_ms", C.c_double),
+                ("heldout_ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _lib = None
 
 
@@ -106,6 +117,12 @@ def load(path: str = LIB_PATH):
     for f in (lib.cox_nll_forward, lib.cox_nll_backward):
         f.argtypes = [C.POINTER(surv_nll_data), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         f.restype = C.c_int
+    lib.cox_lambda_max.argtypes = [C.POINTER(surv_data), C.c_void_p, C.POINTER(C.c_double), C.c_void_p]
+    lib.cox_lambda_max.restype = C.c_int
+    lib.cox_cv_path.argtypes = [C.POINTER(surv_data), C.c_void_p, C.c_int32, C.c_void_p, C.c_int32,
+                                C.POINTER(surv_opts), C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                C.POINTER(surv_cv_info)]
+    lib.cox_cv_path.restype = C.c_int
     lib.surv_strerror.argtypes = [C.c_int]
     lib.surv_strerror.restype = C.c_char_p
     lib.surv_last_error.restype = C.c_char_p
@@ -285,6 +302,37 @@ def loglik_grad_hess_noalloc(data: SurvData, model: str, beta, j: int, precision
                                          C.byref(g), C.byref(h), SURV_PREC[precision], _stream(stream))
     _check(rc)
     return l.value, g.value, h.value
+
+
+def cox_lambda_max(data: SurvData, penalty_factor=None, stream=None):
+    """Smallest L1 strength whose Cox optimum is beta = 0 (computed on the GPU)."""
+    v = C.c_double()
+    _check(load().cox_lambda_max(C.byref(data.c), C.c_void_p(_ptr(penalty_factor)), C.byref(v), _stream(stream)))
+    return v.value
+
+
+def cox_cv_path(data: SurvData, fold_id, nfolds: int, lambdas, penalty="l1", ctas_per_fit=0,
+                allow_not_converged=True, **kw):
+    """Cross-validated Cox penalty path: nlambda x nfolds fits in one batched
+    schedule.  ``fold_id`` int8 [n] (host or device) in data order,
+    ``lambdas`` float64 (host).  Returns a dict with beta [nlambda, nfolds, p],
+    heldout [nlambda, nfolds], cv_mean [nlambda], sweeps [nlambda, nfolds]
+    (numpy), info and the return code."""
+    lam = np.ascontiguousarray(np.asarray(lambdas, dtype=np.float64))
+    L = int(lam.shape[0])
+    F = L * int(nfolds)
+    opts = make_opts(penalty=penalty, **kw)
+    beta = np.empty((L, int(nfolds), data.p), np.float64)
+    held = np.empty((L, int(nfolds)), np.float64)
+    mean = np.empty(L, np.float64)
+    sweeps = np.empty((L, int(nfolds)), np.int32)
+    info = surv_cv_info()
+    rc = load().cox_cv_path(C.byref(data.c), C.c_void_p(_ptr(fold_id)), int(nfolds), C.c_void_p(_ptr(lam)), L,
+                            C.byref(opts), int(ctas_per_fit), C.c_void_p(_ptr(beta)), C.c_void_p(_ptr(held)),
+                            C.c_void_p(_ptr(mean)), C.c_void_p(_ptr(sweeps)), C.byref(info))
+    _check(rc, (SURV_OK, SURV_W_NOT_CONVERGED) if allow_not_converged else (SURV_OK,))
+    assert F == info.nfits
+    return {"beta": beta, "heldout": held, "cv_mean": mean, "sweeps": sweeps, "info": info.as_dict(), "rc": rc}
 
 
 def surv_sort_desc(time, perm=None, stream=None):

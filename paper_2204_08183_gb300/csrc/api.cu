@@ -149,6 +149,111 @@ int map_prep_error(unsigned perr) {
   return SURV_OK;
 }
 
+// Sizes, enums and pointers of a surv_data (SURV_OK or SURV_E_INVALID / NO_EVENTS).
+int check_data(const surv_data* d) {
+  if (!d) { set_error("null data"); return SURV_E_INVALID; }
+  const int64_t n = d->n, p = d->p;
+  if (n < 0 || p < 1 || n > 0x7fffffff || p > 0x7fffffff) { set_error("bad sizes n=%lld p=%lld", (long long)n, (long long)p); return SURV_E_INVALID; }
+  if (d->layout != SURV_CSC && d->layout != SURV_DENSE) { set_error("bad layout"); return SURV_E_INVALID; }
+  if (d->dtype != SURV_F32 && d->dtype != SURV_F64) { set_error("bad dtype"); return SURV_E_INVALID; }
+  if (n == 0) { set_error("no subjects"); return SURV_E_NO_EVENTS; }
+  if (!d->time || !d->status) { set_error("null time/status"); return SURV_E_INVALID; }
+  if (d->layout == SURV_CSC && (!d->col_ptr || !d->row_idx)) { set_error("null CSC arrays"); return SURV_E_INVALID; }
+  if (d->layout == SURV_DENSE && !d->values) { set_error("null dense values"); return SURV_E_INVALID; }
+  return SURV_OK;
+}
+
+// Device views of the data in the working precision prec (0 float, 1 double):
+// caller arrays used in place when they are device memory, else copied; X
+// converted (and dense X padded to a leading dimension that is a multiple
+// of 4) when its dtype or alignment differs.
+struct Staged {
+  const int32_t* time = nullptr;
+  const int8_t* status = nullptr;
+  const int64_t* colptr = nullptr;
+  const int32_t* rowidx = nullptr;
+  const void* vals = nullptr;  // CSC values (null: indicators) or dense X
+  int64_t ld = 0;
+  int64_t nnz = 0;
+  std::vector<int64_t> colptr_h;
+};
+
+int stage_data(const surv_data* d, int prec, surv_workspace* ws, cudaStream_t s, Staged* st, int64_t* launches) {
+  using W = surv_workspace;
+  const int64_t n = d->n, p = d->p;
+  const size_t tsz = prec == 0 ? 4 : 8;
+  int rc;
+  const void *time_d = nullptr, *status_d = nullptr, *colptr_d = nullptr, *rowidx_d = nullptr, *vals_d = nullptr;
+  if ((rc = device_view(ws, W::TIME, d->time, 4 * (size_t)n, s, &time_d))) return rc;
+  if ((rc = device_view(ws, W::STATUS, d->status, (size_t)n, s, &status_d))) return rc;
+  if (d->layout == SURV_CSC) {
+    st->colptr_h.resize(p + 1);
+    if ((rc = to_host(d->col_ptr, 8 * (size_t)(p + 1), st->colptr_h.data(), s))) return rc;
+    if (st->colptr_h[0] != 0) { set_error("col_ptr[0] != 0"); return SURV_E_INDEX; }
+    for (int64_t j = 0; j < p; ++j)
+      if (st->colptr_h[j + 1] < st->colptr_h[j]) { set_error("col_ptr decreases at %lld", (long long)j); return SURV_E_INDEX; }
+    st->nnz = st->colptr_h[p];
+    if ((rc = device_view(ws, W::COLPTR, d->col_ptr, 8 * (size_t)(p + 1), s, &colptr_d))) return rc;
+    if ((rc = device_view(ws, W::ROWIDX, d->row_idx, 4 * (size_t)st->nnz, s, &rowidx_d))) return rc;
+    if (d->values) {
+      const size_t vsz = d->dtype == SURV_F32 ? 4 : 8;
+      if ((rc = device_view(ws, W::VALUES, d->values, vsz * (size_t)st->nnz, s, &vals_d))) return rc;
+      if (d->dtype != prec) {
+        void* conv = nullptr;
+        if ((rc = ensure(ws, W::XD, tsz * (size_t)st->nnz, &conv))) return rc;
+        CUDA_TRY(survgpu::prep_convert_vec(vals_d, d->dtype, st->nnz, conv, prec, s));
+        ++*launches;
+        vals_d = conv;
+      }
+    }
+  }
+  st->ld = n;
+  if (d->layout == SURV_DENSE) {
+    const size_t vsz = d->dtype == SURV_F32 ? 4 : 8;
+    if ((rc = device_view(ws, W::VALUES, d->values, vsz * (size_t)n * (size_t)p, s, &vals_d))) return rc;
+    const bool aligned = ((uintptr_t)vals_d % 16) == 0 && (n % 4) == 0;
+    if (d->dtype != prec || !aligned) {
+      st->ld = (n + 3) / 4 * 4;
+      void* conv = nullptr;
+      if ((rc = ensure(ws, W::XD, tsz * (size_t)st->ld * (size_t)p, &conv))) return rc;
+      CUDA_TRY(survgpu::prep_convert_dense(vals_d, d->dtype, n, p, conv, prec, st->ld, s));
+      ++*launches;
+      vals_d = conv;
+    }
+  }
+  st->time = static_cast<const int32_t*>(time_d);
+  st->status = static_cast<const int8_t*>(status_d);
+  st->colptr = static_cast<const int64_t*>(colptr_d);
+  st->rowidx = static_cast<const int32_t*>(rowidx_d);
+  st->vals = vals_d;
+  return SURV_OK;
+}
+
+// Validation kernels on the staged data and the tie-group count: *K after a
+// synchronisation (ctrl zeroed here; prep errors mapped to return codes).
+int validate_and_count(int model, int layout, int prec, int64_t n, int64_t p, const Staged& st, DevCtrl* ctrl,
+                       surv_workspace* ws, cudaStream_t s, void** blockcnt, int32_t* K, int64_t* launches) {
+  CUDA_TRY(cudaMemsetAsync(ctrl, 0, sizeof(DevCtrl), s));
+  CUDA_TRY(survgpu::prep_check_times(st.time, st.status, n, model, &ctrl->perr, s));
+  ++*launches;
+  if (layout == SURV_CSC)
+    CUDA_TRY(survgpu::prep_check_csc(st.colptr, st.rowidx, st.vals, prec, p, n, &ctrl->perr, s));
+  else
+    CUDA_TRY(survgpu::prep_check_dense(st.vals, prec, st.ld, n, p, &ctrl->perr, s));
+  ++*launches;
+  const int64_t nb = survgpu::prep_end_blocks(n);
+  int rc;
+  if ((rc = ensure(ws, surv_workspace::BLOCKCNT, 4 * (size_t)nb, blockcnt))) return rc;
+  CUDA_TRY(survgpu::prep_count_ends(st.time, n, static_cast<int32_t*>(*blockcnt), &ctrl->K, s));
+  *launches += 2;
+  DevCtrl hc;
+  CUDA_TRY(cudaMemcpyAsync(&hc, ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if ((rc = map_prep_error(hc.perr))) return rc;
+  *K = hc.K;
+  return SURV_OK;
+}
+
 int fit_common(int model, const surv_data* d, const surv_opts* o_in, double* beta_inout, surv_fit_info* info,
                int single_j, double* out_l, double* out_g, double* out_h) {
   g_last_error[0] = '\0';
@@ -199,46 +304,11 @@ int fit_common(int model, const surv_data* d, const surv_opts* o_in, double* bet
 
   // ---------------------------------------------------------- staging
   int rc;
-  const void *time_d = nullptr, *status_d = nullptr, *colptr_d = nullptr, *rowidx_d = nullptr, *vals_d = nullptr;
-  if ((rc = device_view(ws, W::TIME, d->time, 4 * (size_t)n, s, &time_d))) return rc;
-  if ((rc = device_view(ws, W::STATUS, d->status, (size_t)n, s, &status_d))) return rc;
-  int64_t nnz = 0;
-  std::vector<int64_t> colptr_h;
-  if (layout == SURV_CSC) {
-    colptr_h.resize(p + 1);
-    if ((rc = to_host(d->col_ptr, 8 * (size_t)(p + 1), colptr_h.data(), s))) return rc;
-    if (colptr_h[0] != 0) { set_error("col_ptr[0] != 0"); return SURV_E_INDEX; }
-    for (int64_t j = 0; j < p; ++j)
-      if (colptr_h[j + 1] < colptr_h[j]) { set_error("col_ptr decreases at %lld", (long long)j); return SURV_E_INDEX; }
-    nnz = colptr_h[p];
-    if ((rc = device_view(ws, W::COLPTR, d->col_ptr, 8 * (size_t)(p + 1), s, &colptr_d))) return rc;
-    if ((rc = device_view(ws, W::ROWIDX, d->row_idx, 4 * (size_t)nnz, s, &rowidx_d))) return rc;
-    if (d->values) {
-      const size_t vsz = d->dtype == SURV_F32 ? 4 : 8;
-      if ((rc = device_view(ws, W::VALUES, d->values, vsz * (size_t)nnz, s, &vals_d))) return rc;
-      if (d->dtype != prec) {
-        void* conv = nullptr;
-        if ((rc = ensure(ws, W::XD, tsz * (size_t)nnz, &conv))) return rc;
-        CUDA_TRY(survgpu::prep_convert_vec(vals_d, d->dtype, nnz, conv, prec, s));
-        ++launches;
-        vals_d = conv;
-      }
-    }
-  }
-  int64_t ld = n;
-  if (layout == SURV_DENSE) {
-    const size_t vsz = d->dtype == SURV_F32 ? 4 : 8;
-    if ((rc = device_view(ws, W::VALUES, d->values, vsz * (size_t)n * (size_t)p, s, &vals_d))) return rc;
-    const bool aligned = ((uintptr_t)vals_d % 16) == 0 && (n % 4) == 0;
-    if (d->dtype != prec || !aligned) {
-      ld = (n + 3) / 4 * 4;
-      void* conv = nullptr;
-      if ((rc = ensure(ws, W::XD, tsz * (size_t)ld * (size_t)p, &conv))) return rc;
-      CUDA_TRY(survgpu::prep_convert_dense(vals_d, d->dtype, n, p, conv, prec, ld, s));
-      ++launches;
-      vals_d = conv;
-    }
-  }
+  Staged stg;
+  if ((rc = stage_data(d, prec, ws, s, &stg, &launches))) return rc;
+  const void *colptr_d = stg.colptr, *rowidx_d = stg.rowidx, *vals_d = stg.vals;
+  const int64_t ld = stg.ld;
+  const std::vector<int64_t>& colptr_h = stg.colptr_h;
 
   // host copies of beta and penalty factors (p values each)
   std::vector<double> beta_h(p), pf_h(p, 1.0), pen_h(p);
@@ -256,28 +326,12 @@ int fit_common(int model, const surv_data* d, const surv_opts* o_in, double* bet
   void* ctrl_v = nullptr;
   if ((rc = ensure(ws, W::CTRL, sizeof(DevCtrl), &ctrl_v))) return rc;
   DevCtrl* ctrl = static_cast<DevCtrl*>(ctrl_v);
-  CUDA_TRY(cudaMemsetAsync(ctrl, 0, sizeof(DevCtrl), s));
-  const int32_t* time_p = static_cast<const int32_t*>(time_d);
-  const int8_t* status_p = static_cast<const int8_t*>(status_d);
-  CUDA_TRY(survgpu::prep_check_times(time_p, status_p, n, model, &ctrl->perr, s));
-  ++launches;
-  if (layout == SURV_CSC) {
-    CUDA_TRY(survgpu::prep_check_csc(static_cast<const int64_t*>(colptr_d), static_cast<const int32_t*>(rowidx_d),
-                                     vals_d, prec, p, n, &ctrl->perr, s));
-  } else {
-    CUDA_TRY(survgpu::prep_check_dense(vals_d, prec, ld, n, p, &ctrl->perr, s));
-  }
-  ++launches;
+  const int32_t* time_p = stg.time;
+  const int8_t* status_p = stg.status;
   void* blockcnt = nullptr;
-  const int64_t nb = survgpu::prep_end_blocks(n);
-  if ((rc = ensure(ws, W::BLOCKCNT, 4 * (size_t)nb, &blockcnt))) return rc;
-  CUDA_TRY(survgpu::prep_count_ends(time_p, n, static_cast<int32_t*>(blockcnt), &ctrl->K, s));
-  launches += 2;
+  int32_t K = 0;
+  if ((rc = validate_and_count(model, layout, prec, n, p, stg, ctrl, ws, s, &blockcnt, &K, &launches))) return rc;
   DevCtrl hc;
-  CUDA_TRY(cudaMemcpyAsync(&hc, ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, s));
-  CUDA_TRY(cudaStreamSynchronize(s));
-  if ((rc = map_prep_error(hc.perr))) return rc;
-  const int32_t K = hc.K;
 
   // ---------------------------------------------------------- tables
   void *gend, *dk, *ck, *Gk, *rec, *e, *eta, *w2 = nullptr, *wk0, *woff = nullptr, *dTx, *beta, *width, *pen, *slots;
@@ -481,6 +535,332 @@ int fit_common(int model, const surv_data* d, const surv_opts* o_in, double* bet
   return hc.out[survgpu::OUT_CONVERGED] != 0.0 ? SURV_OK : SURV_W_NOT_CONVERGED;
 }
 
+// ---------------------------------------------------------------- lambda_max
+int lambda_max_impl(const surv_data* d, const double* pf_in, double* out, void* stream) {
+  g_last_error[0] = '\0';
+  if (!out) { set_error("null lambda_max"); return SURV_E_INVALID; }
+  int rc;
+  if ((rc = check_data(d))) return rc;
+  const int64_t n = d->n, p = d->p;
+  const int layout = d->layout;
+  const int prec = d->dtype == SURV_F32 ? 0 : 1;  // the data's own precision; the sums are FP64
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  surv_workspace ws;
+  struct Free { surv_workspace* w; ~Free() { free_all(w); } } fr{&ws};
+  using W = surv_workspace;
+  CUDA_TRY(cudaGetDevice(&ws.device));
+  int64_t launches = 0;
+  Staged stg;
+  if ((rc = stage_data(d, prec, &ws, s, &stg, &launches))) return rc;
+  const double* pf_d = nullptr;
+  if (pf_in) {
+    std::vector<double> pf_h(p);
+    if ((rc = to_host(pf_in, 8 * (size_t)p, pf_h.data(), s))) return rc;
+    for (int64_t j = 0; j < p; ++j)
+      if (!std::isfinite(pf_h[j]) || pf_h[j] < 0.0) { set_error("invalid penalty factor at %lld", (long long)j); return SURV_E_NONFINITE; }
+    const void* v = nullptr;
+    if ((rc = device_view(&ws, W::PF, pf_in, 8 * (size_t)p, s, &v))) return rc;
+    pf_d = static_cast<const double*>(v);
+  }
+  void* ctrl_v = nullptr;
+  if ((rc = ensure(&ws, W::CTRL, sizeof(DevCtrl), &ctrl_v))) return rc;
+  DevCtrl* ctrl = static_cast<DevCtrl*>(ctrl_v);
+  void* blockcnt = nullptr;
+  int32_t K = 0;
+  if ((rc = validate_and_count(SURV_COX, layout, prec, n, p, stg, ctrl, &ws, s, &blockcnt, &K, &launches))) return rc;
+  void *gend, *dk, *ck, *lam, *r, *g;
+  if ((rc = ensure(&ws, W::GEND, 4 * (size_t)K, &gend))) return rc;
+  if ((rc = ensure(&ws, W::DK, 4 * (size_t)K, &dk))) return rc;
+  if ((rc = ensure(&ws, W::CK, 4 * (size_t)K, &ck))) return rc;
+  if ((rc = ensure(&ws, W::LM_LAM, 8 * (size_t)K, &lam))) return rc;
+  if ((rc = ensure(&ws, W::LM_R, 8 * (size_t)n, &r))) return rc;
+  if ((rc = ensure(&ws, W::LM_G, 8 * (size_t)(p + 1), &g))) return rc;
+  CUDA_TRY(survgpu::prep_write_ends(stg.time, n, static_cast<const int32_t*>(blockcnt), static_cast<int32_t*>(gend), s));
+  CUDA_TRY(survgpu::prep_group_stats(static_cast<int32_t*>(gend), K, stg.status, static_cast<int32_t*>(dk),
+                                     static_cast<int32_t*>(ck), &ctrl->total_events, s));
+  double* gd = static_cast<double*>(g);
+  CUDA_TRY(survgpu::lambda_max_device(layout, prec, stg.colptr, stg.rowidx, stg.vals, stg.ld, n, p, stg.status,
+                                      static_cast<const int32_t*>(gend), static_cast<const int32_t*>(dk), K, pf_d,
+                                      static_cast<double*>(lam), static_cast<double*>(r), gd, gd + p, s));
+  DevCtrl hc;
+  double v = 0.0;
+  CUDA_TRY(cudaMemcpyAsync(&hc, ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(&v, gd + p, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (hc.total_events <= 0) { set_error("no events"); return SURV_E_NO_EVENTS; }
+  *out = v;
+  return SURV_OK;
+}
+
+// ------------------------------------------------------ cross-validated path
+struct CvCtrl {
+  unsigned perr;
+  unsigned done;         // fits that have stopped
+  int32_t best;          // index of the chosen lambda
+  int32_t pad;
+  int32_t events[128];   // training events per fold
+};
+
+// CTAs per fit when the caller leaves it to the library: the smallest count
+// whose total over all fits fills the co-resident slots to at least 90 %
+// in the last wave, within the rows available.
+int cv_ctas_per_fit(int F, int Gmax, int max_by_rows) {
+  const int lim = std::max(1, std::min(Gmax, max_by_rows));
+  for (int g = 1; g <= lim; ++g) {
+    const int64_t tot = (int64_t)g * F;
+    const int64_t waves = (tot + Gmax - 1) / Gmax;
+    if ((double)tot / (double)(waves * Gmax) >= 0.9) return g;
+  }
+  return lim;
+}
+
+int cv_impl(const surv_data* d, const int8_t* fold_id, int nfolds, const double* lambdas, int nlambda,
+            const surv_opts* o_in, int ctas_per_fit, double* beta_out, double* heldout_out, double* cv_mean_out,
+            int32_t* sweeps_out, surv_cv_info* info) {
+  g_last_error[0] = '\0';
+  surv_opts o;
+  if (o_in) o = *o_in; else surv_opts_default(&o);
+  int rc;
+  if ((rc = check_data(d))) return rc;
+  if (!fold_id || !lambdas || !beta_out) { set_error("null fold_id, lambdas or beta_out"); return SURV_E_INVALID; }
+  if (nfolds < 1 || nfolds > 127 || nlambda < 1 || (int64_t)nfolds * nlambda > 65535) {
+    set_error("bad nfolds=%d / nlambda=%d", nfolds, nlambda);
+    return SURV_E_INVALID;
+  }
+  if (ctas_per_fit < 0) { set_error("negative ctas_per_fit"); return SURV_E_INVALID; }
+  if (o.penalty < 0 || o.penalty > 2 || o.precision < 0 || o.precision > 1) { set_error("bad penalty/precision"); return SURV_E_INVALID; }
+  if (!(o.tol >= 0.0) || o.max_sweeps < 0) { set_error("bad tol/max_sweeps"); return SURV_E_INVALID; }
+  const int64_t n = d->n, p = d->p;
+  const int F = nfolds * nlambda;
+  const int layout = d->layout;
+  const int prec = o.precision;
+  const size_t tsz = prec == 0 ? 4 : 8;
+  constexpr int M = 3;
+  cudaStream_t s = static_cast<cudaStream_t>(o.stream);
+  int64_t launches = 0;
+  WsGuard guard;
+  surv_workspace* ws = o.workspace;
+  if (!ws) {
+    ws = new surv_workspace();
+    guard.ws = ws;
+    guard.owned = true;
+  }
+  CUDA_TRY(cudaGetDevice(&ws->device));
+  using W = surv_workspace;
+
+  // lambdas and penalty factors (host copies; pen[f][j] = lambda_l * pf_j)
+  std::vector<double> lam_h(nlambda), pf_h(p, 1.0);
+  if ((rc = to_host(lambdas, 8 * (size_t)nlambda, lam_h.data(), s))) return rc;
+  for (double l : lam_h)
+    if (!std::isfinite(l) || l < 0.0) { set_error("lambdas must be finite and >= 0"); return SURV_E_INVALID; }
+  if (o.penalty_factor && (rc = to_host(o.penalty_factor, 8 * (size_t)p, pf_h.data(), s))) return rc;
+  for (int64_t j = 0; j < p; ++j)
+    if (!std::isfinite(pf_h[j]) || pf_h[j] < 0.0) { set_error("invalid penalty factor at %lld", (long long)j); return SURV_E_NONFINITE; }
+
+  // grid of each fit
+  int Gmax = 0, wpc = 0;
+  CUDA_TRY(survgpu::graph_grid_size(SURV_COX, layout, prec, &Gmax, &wpc));
+  if (Gmax < 1) { set_error("CCD kernels do not fit on the device"); return SURV_E_CUDA; }
+  const int64_t nwords = (n + 31) / 32;
+  const int max_by_rows = (int)std::min<int64_t>(Gmax, std::max<int64_t>(1, nwords / wpc));
+  const int G = ctas_per_fit > 0 ? std::min(ctas_per_fit, Gmax) : cv_ctas_per_fit(F, Gmax, max_by_rows);
+  const int32_t nwarps = G * wpc;
+  const int32_t wpw = (int32_t)((nwords + nwarps - 1) / nwarps);
+  const int64_t rows_per_warp = (int64_t)wpw * 32;
+
+  // staging and validation
+  Staged stg;
+  if ((rc = stage_data(d, prec, ws, s, &stg, &launches))) return rc;
+  void* ctrl_v = nullptr;
+  if ((rc = ensure(ws, W::CTRL, sizeof(DevCtrl), &ctrl_v))) return rc;
+  DevCtrl* ctrl = static_cast<DevCtrl*>(ctrl_v);
+  void* blockcnt = nullptr;
+  int32_t K = 0;
+  if ((rc = validate_and_count(SURV_COX, layout, prec, n, p, stg, ctrl, ws, s, &blockcnt, &K, &launches))) return rc;
+  const void* fold_v = nullptr;
+  if ((rc = device_view(ws, W::CV_FOLD, fold_id, (size_t)n, s, &fold_v))) return rc;
+  const int8_t* fold_d = static_cast<const int8_t*>(fold_v);
+
+  // shared tables, per-fold tables, per-fit state
+  void *gend, *dk, *ck, *wk0, *woff = nullptr, *dkf, *dtxf, *cvc_v;
+  void *e, *eta, *rec, *wt, *agg, *part, *gctl, *beta, *width, *pen, *out, *fits, *den, *held, *mean;
+  if ((rc = ensure(ws, W::GEND, 4 * (size_t)K, &gend))) return rc;
+  if ((rc = ensure(ws, W::DK, 4 * (size_t)K, &dk))) return rc;
+  if ((rc = ensure(ws, W::CK, 4 * (size_t)K, &ck))) return rc;
+  if ((rc = ensure(ws, W::WK0, 4 * (size_t)(nwarps + 1), &wk0))) return rc;
+  if (layout == SURV_CSC && (rc = ensure(ws, W::WOFF, 4 * (size_t)p * (nwarps + 1), &woff))) return rc;
+  if ((rc = ensure(ws, W::CV_DK, 4 * (size_t)nfolds * K, &dkf))) return rc;
+  if ((rc = ensure(ws, W::CV_DTX, 8 * (size_t)nfolds * p, &dtxf))) return rc;
+  if ((rc = ensure(ws, W::CV_CTRL, sizeof(CvCtrl), &cvc_v))) return rc;
+  if ((rc = ensure(ws, W::CV_E, tsz * (size_t)F * n, &e))) return rc;
+  if ((rc = ensure(ws, W::CV_ETA, 8 * (size_t)F * n, &eta))) return rc;
+  if ((rc = ensure(ws, W::CV_REC, 8 * (size_t)F * K * M, &rec))) return rc;
+  if ((rc = ensure(ws, W::CV_WT, 8 * (size_t)F * M * nwarps, &wt))) return rc;
+  if ((rc = ensure(ws, W::CV_AGG, 8 * (size_t)F * survgpu::kRep * M * G, &agg))) return rc;
+  if ((rc = ensure(ws, W::CV_PART, 8 * (size_t)F * 3 * G, &part))) return rc;
+  if ((rc = ensure(ws, W::CV_GCTL, sizeof(survgpu::GraphCtl) * (size_t)F, &gctl))) return rc;
+  if ((rc = ensure(ws, W::CV_BETA, 8 * (size_t)F * p, &beta))) return rc;
+  if ((rc = ensure(ws, W::CV_WIDTH, 8 * (size_t)F * p, &width))) return rc;
+  if ((rc = ensure(ws, W::CV_PEN, 8 * (size_t)F * p, &pen))) return rc;
+  if ((rc = ensure(ws, W::CV_OUT, 8 * (size_t)F * survgpu::OUT_COUNT, &out))) return rc;
+  if ((rc = ensure(ws, W::CV_FITS, sizeof(CcdParams) * (size_t)F, &fits))) return rc;
+  if ((rc = ensure(ws, W::CV_DEN, 8 * (size_t)F * K, &den))) return rc;
+  if ((rc = ensure(ws, W::CV_HELD, 8 * (size_t)F, &held))) return rc;
+  if ((rc = ensure(ws, W::CV_MEAN, 8 * (size_t)nlambda, &mean))) return rc;
+  CvCtrl* cvc = static_cast<CvCtrl*>(cvc_v);
+
+  CUDA_TRY(cudaMemsetAsync(cvc, 0, sizeof(CvCtrl), s));
+  CUDA_TRY(survgpu::cv_check_folds(fold_d, n, nfolds, &cvc->perr, s));
+  CUDA_TRY(survgpu::prep_write_ends(stg.time, n, static_cast<const int32_t*>(blockcnt), static_cast<int32_t*>(gend), s));
+  CUDA_TRY(survgpu::prep_group_stats(static_cast<int32_t*>(gend), K, stg.status, static_cast<int32_t*>(dk),
+                                     static_cast<int32_t*>(ck), &ctrl->total_events, s));
+  CUDA_TRY(survgpu::cv_fold_stats(static_cast<int32_t*>(gend), K, stg.status, fold_d, nfolds,
+                                  static_cast<int32_t*>(dkf), cvc->events, s));
+  CUDA_TRY(survgpu::cv_dtx(layout == SURV_CSC ? 0 : 1, prec, stg.colptr, stg.rowidx, stg.vals, stg.ld, n, p,
+                           stg.status, fold_d, nfolds, static_cast<double*>(dtxf), s));
+  if (layout == SURV_CSC) {
+    CUDA_TRY(survgpu::prep_warp_offsets(stg.colptr, stg.rowidx, p, n, nwarps, rows_per_warp,
+                                        static_cast<int32_t*>(woff), s));
+    ++launches;
+  }
+  CUDA_TRY(survgpu::prep_warp_groups(static_cast<int32_t*>(gend), K, n, nwarps, rows_per_warp,
+                                     static_cast<int32_t*>(wk0), s));
+  CUDA_TRY(survgpu::cv_init(prec, n, fold_d, nfolds, F, e, eta, s));
+  launches += 7;
+  std::vector<double> pen_h((size_t)F * p);
+  for (int f = 0; f < F; ++f)
+    for (int64_t j = 0; j < p; ++j) pen_h[(size_t)f * p + j] = lam_h[f / nfolds] * pf_h[j];
+  CUDA_TRY(cudaMemcpyAsync(pen, pen_h.data(), 8 * pen_h.size(), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemsetAsync(beta, 0, 8 * (size_t)F * p, s));
+  CUDA_TRY(survgpu::prep_fill_f64(static_cast<double*>(width), 1.0, (int64_t)F * p, s));
+  CUDA_TRY(cudaMemsetAsync(gctl, 0, sizeof(survgpu::GraphCtl) * (size_t)F, s));
+  CUDA_TRY(cudaMemsetAsync(out, 0, 8 * (size_t)F * survgpu::OUT_COUNT, s));
+  ++launches;
+  CvCtrl hcv;
+  DevCtrl hc;
+  CUDA_TRY(cudaMemcpyAsync(&hcv, cvc, sizeof(CvCtrl), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(&hc, ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (hcv.perr & survgpu::PREP_FOLD) { set_error("fold_id outside [0, %d)", nfolds); return SURV_E_INVALID; }
+  if (hc.total_events <= 0) { set_error("no events"); return SURV_E_NO_EVENTS; }
+  for (int k = 0; k < nfolds; ++k)
+    if (hcv.events[k] <= 0) { set_error("no events outside fold %d", k); return SURV_E_NO_EVENTS; }
+
+  // per-fit parameters
+  CcdParams P;
+  std::memset(&P, 0, sizeof(P));
+  P.n = n;
+  P.ld = stg.ld;
+  P.p = (int32_t)p;
+  P.K = K;
+  P.G = G;
+  P.wpc = wpc;
+  P.wpw = wpw;
+  P.nwarps = nwarps;
+  P.gend = static_cast<const int32_t*>(gend);
+  P.wk0 = static_cast<const int32_t*>(wk0);
+  P.col_ptr = stg.colptr;
+  P.row_idx = stg.rowidx;
+  P.values = layout == SURV_CSC ? stg.vals : nullptr;
+  P.woff = static_cast<const int32_t*>(woff);
+  P.X = layout == SURV_DENSE ? stg.vals : nullptr;
+  P.penalty = o.penalty;
+  P.max_sweeps = o.max_sweeps;
+  P.tol = o.tol;
+  P.single_j = -1;
+  P.withhold_cta = -1;
+  P.done_count = &cvc->done;
+  P.nfit = F;
+  P.fold_id = fold_d;
+  std::vector<CcdParams> fits_h(F);
+  for (int f = 0; f < F; ++f) {
+    const int k = f % nfolds;
+    CcdParams& Q = fits_h[f];
+    Q = P;
+    Q.fold = k;
+    Q.dk = static_cast<const int32_t*>(dkf) + (size_t)k * K;
+    Q.dTx = static_cast<const double*>(dtxf) + (size_t)k * p;
+    Q.e = static_cast<char*>(e) + tsz * (size_t)f * n;
+    Q.eta = static_cast<char*>(eta) + 8 * (size_t)f * n;
+    Q.rec = static_cast<char*>(rec) + 8 * (size_t)f * K * M;
+    Q.wt = static_cast<uint64_t*>(wt) + (size_t)f * M * nwarps;
+    Q.agg = static_cast<uint64_t*>(agg) + (size_t)f * survgpu::kRep * M * G;
+    Q.slot_part = reinterpret_cast<unsigned*>(static_cast<uint64_t*>(part) + (size_t)f * 3 * G);
+    Q.gctl = static_cast<survgpu::GraphCtl*>(gctl) + f;
+    Q.beta = static_cast<double*>(beta) + (size_t)f * p;
+    Q.width = static_cast<double*>(width) + (size_t)f * p;
+    Q.pen = static_cast<const double*>(pen) + (size_t)f * p;
+    Q.out = static_cast<double*>(out) + (size_t)f * survgpu::OUT_COUNT;
+    Q.fits = nullptr;
+  }
+  CUDA_TRY(cudaMemcpyAsync(fits, fits_h.data(), sizeof(CcdParams) * (size_t)F, cudaMemcpyHostToDevice, s));
+  CcdParams P0 = fits_h[0];
+  P0.fits = static_cast<const CcdParams*>(fits);
+
+  struct Events {
+    cudaEvent_t a = nullptr, b = nullptr, c = nullptr;
+    ~Events() {
+      if (a) cudaEventDestroy(a);
+      if (b) cudaEventDestroy(b);
+      if (c) cudaEventDestroy(c);
+    }
+  } ev;
+  CUDA_TRY(cudaEventCreate(&ev.a));
+  CUDA_TRY(cudaEventCreate(&ev.b));
+  CUDA_TRY(cudaEventCreate(&ev.c));
+  int replays = 0, glaunches = 0;
+  CUDA_TRY(survgpu::graph_init(P0, s));
+  ++launches;
+  CUDA_TRY(survgpu::run_ccd_graph(SURV_COX, layout == SURV_CSC ? 0 : 1, prec, P0, s,
+                                  o_in && o_in->workspace ? &ws->graph : nullptr, ev.a, &replays, &glaunches));
+  launches += glaunches;
+  CUDA_TRY(cudaEventRecord(ev.b, s));
+  CUDA_TRY(survgpu::cv_heldout(prec, n, stg.time, stg.status, fold_d, nfolds, F, eta, static_cast<const int32_t*>(dk),
+                               static_cast<const int32_t*>(dkf), K, static_cast<double*>(den),
+                               static_cast<double*>(held), s));
+  CUDA_TRY(survgpu::cv_select(static_cast<const double*>(held), nlambda, nfolds, static_cast<double*>(mean),
+                              &cvc->best, s));
+  launches += 2;
+  CUDA_TRY(cudaEventRecord(ev.c, s));
+  std::vector<double> out_h((size_t)F * survgpu::OUT_COUNT);
+  CUDA_TRY(cudaMemcpyAsync(out_h.data(), out, 8 * out_h.size(), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(&hcv, cvc, sizeof(CvCtrl), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (hcv.done != (unsigned)F) {
+    set_error("%u of %d fits stopped after %d sweep replays", hcv.done, F, replays);
+    return SURV_E_CUDA;
+  }
+  CUDA_TRY(cudaMemcpyAsync(beta_out, beta, 8 * (size_t)F * p, cudaMemcpyDefault, s));
+  if (heldout_out) CUDA_TRY(cudaMemcpyAsync(heldout_out, held, 8 * (size_t)F, cudaMemcpyDefault, s));
+  if (cv_mean_out) CUDA_TRY(cudaMemcpyAsync(cv_mean_out, mean, 8 * (size_t)nlambda, cudaMemcpyDefault, s));
+  std::vector<int32_t> sw((size_t)F);
+  int conv = 0, maxsw = 0;
+  for (int f = 0; f < F; ++f) {
+    sw[f] = (int32_t)out_h[(size_t)f * survgpu::OUT_COUNT + survgpu::OUT_SWEEPS];
+    conv += out_h[(size_t)f * survgpu::OUT_COUNT + survgpu::OUT_CONVERGED] != 0.0;
+    maxsw = std::max(maxsw, sw[f]);
+  }
+  if (sweeps_out) CUDA_TRY(cudaMemcpyAsync(sweeps_out, sw.data(), 4 * (size_t)F, cudaMemcpyDefault, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->nfits = F;
+    info->best_lambda = hcv.best;
+    info->max_sweeps_used = maxsw;
+    info->fits_converged = conv;
+    info->graph_replays = replays;
+    info->ctas_per_fit = G;
+    info->kernel_launches = launches;
+    info->n_groups = K;
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, ev.a, ev.b));
+    info->ccd_kernel_ms = ms;
+    CUDA_TRY(cudaEventElapsedTime(&ms, ev.b, ev.c));
+    info->heldout_ms = ms;
+  }
+  return conv == F ? SURV_OK : SURV_W_NOT_CONVERGED;
+}
+
 }  // namespace
 
 namespace survgpu {
@@ -597,6 +977,17 @@ int surv_groups(const int32_t* time, const int8_t* status, int64_t n, int64_t ma
   if (Gk_out) CUDA_TRY(cudaMemcpyAsync(Gk_out, Gk, 8 * (size_t)K, cudaMemcpyDefault, s));
   CUDA_TRY(cudaStreamSynchronize(s));
   return SURV_OK;
+}
+
+int cox_lambda_max(const surv_data* data, const double* penalty_factor, double* lambda_max, void* stream) {
+  return lambda_max_impl(data, penalty_factor, lambda_max, stream);
+}
+
+int cox_cv_path(const surv_data* data, const int8_t* fold_id, int32_t nfolds, const double* lambdas,
+                int32_t nlambda, const surv_opts* opts, int32_t ctas_per_fit, double* beta_out, double* heldout,
+                double* cv_mean, int32_t* sweeps, surv_cv_info* info) {
+  return cv_impl(data, fold_id, nfolds, lambdas, nlambda, opts, ctas_per_fit, beta_out, heldout, cv_mean, sweeps,
+                 info);
 }
 
 const char* surv_strerror(int code) {

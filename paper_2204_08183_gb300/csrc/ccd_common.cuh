@@ -31,17 +31,19 @@ template <> struct Vec<double> {
 };
 
 // eta storage: float-float (float2) in the FP32 mode, double in the FP64 mode
-__device__ __forceinline__ void eta_axpy(float2* eta, float* e, int64_t i, float x, ff delta) {
+// (a subject held out of a cross-validation fit keeps e = 0)
+__device__ __forceinline__ void eta_axpy(float2* eta, float* e, int64_t i, float x, ff delta, bool held = false) {
   float2 q = eta[i];
   ff v = ff_add({q.x, q.y}, ff_mul_f(delta, x));
   eta[i] = make_float2(v.hi, v.lo);
   float ev = expf(v.hi);
-  e[i] = fmaf(ev, v.lo, ev);  // exp(hi + lo) to first order in lo
+  e[i] = held ? 0.f : fmaf(ev, v.lo, ev);  // exp(hi + lo) to first order in lo
 }
-__device__ __forceinline__ void eta_axpy(double* eta, double* e, int64_t i, double x, double delta) {
+__device__ __forceinline__ void eta_axpy(double* eta, double* e, int64_t i, double x, double delta,
+                                         bool held = false) {
   double v = eta[i] + x * delta;
   eta[i] = v;
-  e[i] = exp(v);
+  e[i] = held ? 0.0 : exp(v);
 }
 
 // 8-byte exchange payload words: float-float as (hi, lo), double as its bits
@@ -418,7 +420,9 @@ __device__ __forceinline__ void cta_update(const CcdParams& P, int j, int w_lo, 
 // The same update restricted to the rows of one warp (CSC: the nonzeros of
 // column j between the warp's offsets; dense: rows [r_lo, r_hi)).  Only the
 // calling warp's lanes take part; a __syncwarp after it makes the new e
-// visible to the warp's own pass.
+// visible to the warp's own pass.  In a batched cross-validation fit the
+// subjects of the fit's fold keep e = 0 (their eta is still updated: it is
+// x_i^T beta for the held-out score).
 template <int LAYOUT, typename T>
 __device__ __forceinline__ void warp_update(const CcdParams& P, int j, int gw, int64_t r_lo, int64_t r_hi,
                                             double applied, ff delta) {
@@ -451,22 +455,27 @@ __device__ __forceinline__ void warp_update(const CcdParams& P, int j, int gw, i
           const ff v = ff_add({qq[u].x, qq[u].y}, ff_mul_f(delta, xx[u]));
           etap[rr[u]] = make_float2(v.hi, v.lo);
           const float ev = expf(v.hi);
-          ep[rr[u]] = fmaf(ev, v.lo, ev);
+          // subjects held out of a cross-validation fit stay out of every risk set
+          ep[rr[u]] = (P.fold_id && P.fold_id[rr[u]] == P.fold) ? 0.f : fmaf(ev, v.lo, ev);
         }
       }
     } else {
-      for (int i = a + lane; i < b; i += 32)
-        eta_axpy(reinterpret_cast<double*>(P.eta), reinterpret_cast<double*>(P.e), ri[i],
-                 vals ? (double)vals[i] : 1.0, applied);
+      for (int i = a + lane; i < b; i += 32) {
+        const int r = ri[i];
+        eta_axpy(reinterpret_cast<double*>(P.eta), reinterpret_cast<double*>(P.e), r,
+                 vals ? (double)vals[i] : 1.0, applied, P.fold_id && P.fold_id[r] == P.fold);
+      }
     }
   } else {
     const T* xcol = reinterpret_cast<const T*>(P.X) + (size_t)j * P.ld;
     if constexpr (sizeof(T) == 4) {
       for (int64_t i = r_lo + lane; i < r_hi; i += 32)
-        eta_axpy(reinterpret_cast<float2*>(P.eta), reinterpret_cast<float*>(P.e), i, (float)xcol[i], delta);
+        eta_axpy(reinterpret_cast<float2*>(P.eta), reinterpret_cast<float*>(P.e), i, (float)xcol[i], delta,
+                 P.fold_id && P.fold_id[i] == P.fold);
     } else {
       for (int64_t i = r_lo + lane; i < r_hi; i += 32)
-        eta_axpy(reinterpret_cast<double*>(P.eta), reinterpret_cast<double*>(P.e), i, (double)xcol[i], applied);
+        eta_axpy(reinterpret_cast<double*>(P.eta), reinterpret_cast<double*>(P.e), i, (double)xcol[i], applied,
+                 P.fold_id && P.fold_id[i] == P.fold);
     }
   }
   __syncwarp();

@@ -21,6 +21,12 @@
 // rows, so the update of q needs no barrier before the pass.  Launches use
 // programmatic dependent launch: loads of static tables are issued before
 // griddepcontrol.wait, which hides most of the launch gap.
+//
+// Batched fits (cross-validation x lambda path, Section 2.8): the same two
+// kernels run every fit at once, fit f on blockIdx.y with its own
+// parameters (CcdParams::fits[f], copied to shared memory at the start of
+// each CTA).  Fits stop independently; each one counts itself into a device
+// counter when it stops, and the host replays the sweep until all have.
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
@@ -78,8 +84,22 @@ __device__ __forceinline__ LineView load_line(const GraphCtl* ctl, int c) {
   return v;
 }
 
-// Fill every control line for the first coordinate of a fit.
-__global__ void k_graph_init(const __grid_constant__ CcdParams P) {
+// Per-fit parameters of a batched launch, read once per CTA into shared
+// memory (the table is written before the fit starts: it may be read before
+// the wait on the previous kernel).
+__device__ __forceinline__ void load_fit(CcdParams& dst, const CcdParams& P0) {
+  static_assert(sizeof(CcdParams) % 8 == 0, "CcdParams is copied in 8-byte words");
+  constexpr int W = sizeof(CcdParams) / 8;
+  const unsigned long long* src = reinterpret_cast<const unsigned long long*>(P0.fits + blockIdx.y);
+  unsigned long long* d = reinterpret_cast<unsigned long long*>(&dst);
+  for (int i = threadIdx.x; i < W; i += blockDim.x) d[i] = __ldg(src + i);
+  __syncthreads();
+}
+
+// Fill every control line for the first coordinate of a fit (of fit
+// blockIdx.y in a batched launch).
+__global__ void k_graph_init(const __grid_constant__ CcdParams P0) {
+  const CcdParams& P = P0.fits ? P0.fits[blockIdx.y] : P0;
   const int r = threadIdx.x;
   if (r >= kRep) return;
   CtlLine* L = &P.gctl->line[r];
@@ -97,9 +117,9 @@ __global__ void k_graph_init(const __grid_constant__ CcdParams P) {
   L->eta_updates = 0;
 }
 
-template <int MODEL, int LAYOUT, typename T>
+template <int MODEL, int LAYOUT, typename T, bool BATCH>
 __global__ void __launch_bounds__(GCfg<MODEL, LAYOUT>::NT, GCfg<MODEL, LAYOUT>::MINB)
-    k_pass(const __grid_constant__ CcdParams P, int j) {
+    k_pass(const __grid_constant__ CcdParams P0, int j) {
   using A = typename AccOf<T>::type;
   using C = Cfg<MODEL, LAYOUT, T>;
   constexpr int M = C::M;
@@ -107,6 +127,9 @@ __global__ void __launch_bounds__(GCfg<MODEL, LAYOUT>::NT, GCfg<MODEL, LAYOUT>::
   __shared__ int s_stop;
   __shared__ double s_applied;
   __shared__ float s_delta[2];
+  __shared__ CcdParams s_fit;
+  if (BATCH) load_fit(s_fit, P0);
+  const CcdParams& P = BATCH ? s_fit : P0;
 
   const int tid = threadIdx.x;
   const int lane = tid & 31;
@@ -180,8 +203,8 @@ __global__ void __launch_bounds__(GCfg<MODEL, LAYOUT>::NT, GCfg<MODEL, LAYOUT>::
 // ends), the several sums of each stage share one reduction tree, and the
 // common path (at most one group end per thread) has one block barrier
 // before the partials.
-template <int MODEL, int LAYOUT, typename T>
-__global__ void __launch_bounds__(kTransThreads) k_trans(const __grid_constant__ CcdParams P, int j) {
+template <int MODEL, int LAYOUT, typename T, bool BATCH>
+__global__ void __launch_bounds__(kTransThreads) k_trans(const __grid_constant__ CcdParams P0, int j) {
   using A = typename AccOf<T>::type;
   constexpr int M = MODEL == 0 ? 3 : 6;
   constexpr int NA = MODEL == 0 ? M : 2 * M;  // prefix sums (+ totals for Fine-Gray)
@@ -190,8 +213,12 @@ __global__ void __launch_bounds__(kTransThreads) k_trans(const __grid_constant__
   __shared__ A s_base[kMaxWarpsPerCta][M];
   __shared__ A s_red[kTransWarps][3];
   __shared__ int s_last;
+  __shared__ int s_stopped;
   __shared__ double s_lin[2];
   __shared__ double s_next[4];
+  __shared__ CcdParams s_fit;
+  if (BATCH) load_fit(s_fit, P0);
+  const CcdParams& P = BATCH ? s_fit : P0;
 
   GraphCtl* ctl = P.gctl;
   const int tid = threadIdx.x;
@@ -223,7 +250,10 @@ __global__ void __launch_bounds__(kTransThreads) k_trans(const __grid_constant__
   // ------------------ every load of this kernel's inputs, in one round trip
   // (thread 0 also reads the control line: stop flag and the scalars of j)
   LineView lv;
-  if (tid == 0) lv = load_line(ctl, c);
+  if (tid == 0) {
+    lv = load_line(ctl, c);
+    s_stopped = lv.stop;
+  }
   const uint64_t* agg = P.agg + (size_t)(c % kRep) * M * G;
   // warp of this thread's group end (relative to the CTA); the pass kernel
   // stored each warp's offset inside the CTA in wt
@@ -267,6 +297,7 @@ __global__ void __launch_bounds__(kTransThreads) k_trans(const __grid_constant__
       for (int i = 0; i < NA; ++i) s_wp[w][i] = r[i];
   }
   __syncthreads();
+  if (BATCH && s_stopped) return;  // this fit has stopped (the others go on)
   // prefix before CTA c and (Fine-Gray) grand totals, same order everywhere
   A T_c[M], tot[M];
 #pragma unroll
@@ -423,6 +454,7 @@ __global__ void __launch_bounds__(kTransThreads) k_trans(const __grid_constant__
           P.out[OUT_ETA_UPDATES] = (double)lv.eta_updates;
           P.out[OUT_PASSES] = (double)out.passes;
           ctl->done = 1;
+          if (P.done_count) atomicAdd(P.done_count, 1u);
         }
       }
       double bnew = lv.beta, wnew = lv.width;
@@ -484,7 +516,8 @@ cudaError_t grid_graph(int* G, int* wpc) {
   cudaError_t st = cudaGetDevice(&dev);
   if (st != cudaSuccess) return st;
   if ((st = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return st;
-  if ((st = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pass<MODEL, LAYOUT, T>, GC::NT, 0)) != cudaSuccess)
+  if ((st = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pass<MODEL, LAYOUT, T, false>, GC::NT, 0)) !=
+      cudaSuccess)
     return st;
   if (occ < 1) return cudaErrorLaunchOutOfResources;
   *G = sms * std::min(occ, GC::MINB);
@@ -501,17 +534,34 @@ cudaError_t capture_sweep(const CcdParams& P, bool pdl, cudaStream_t cs, cudaGra
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = pdl ? 1 : 0;
   cudaLaunchConfig_t cp = {};
-  cp.gridDim = dim3(P.G);
+  cp.gridDim = dim3(P.G, P.nfit > 0 ? P.nfit : 1);
   cp.blockDim = dim3(GC::NT);
   cp.stream = cs;
   cp.attrs = attr;
   cp.numAttrs = 1;
   cudaLaunchConfig_t ct = cp;
   ct.blockDim = dim3(kTransThreads);
+  // batched fits: Cox only (the censoring weights of Fine-Gray would have
+  // to be re-estimated on each training set)
+  auto kp = k_pass<MODEL, LAYOUT, T, false>;
+  auto kt = k_trans<MODEL, LAYOUT, T, false>;
+  if constexpr (MODEL == 0) {
+    if (P.nfit > 0) {
+      kp = k_pass<MODEL, LAYOUT, T, true>;
+      kt = k_trans<MODEL, LAYOUT, T, true>;
+    }
+  } else {
+    if (P.nfit > 0) {
+      cudaGraph_t junk = nullptr;
+      cudaStreamEndCapture(cs, &junk);
+      if (junk) cudaGraphDestroy(junk);
+      return cudaErrorInvalidValue;
+    }
+  }
   cudaError_t lst = cudaSuccess;
   for (int j = 0; j < P.p && lst == cudaSuccess; ++j) {
-    lst = cudaLaunchKernelEx(&cp, k_pass<MODEL, LAYOUT, T>, P, j);
-    if (lst == cudaSuccess) lst = cudaLaunchKernelEx(&ct, k_trans<MODEL, LAYOUT, T>, P, j);
+    lst = cudaLaunchKernelEx(&cp, kp, P, j);
+    if (lst == cudaSuccess) lst = cudaLaunchKernelEx(&ct, kt, P, j);
   }
   st = cudaStreamEndCapture(cs, g);
   return lst != cudaSuccess ? lst : st;
@@ -544,7 +594,7 @@ cudaError_t graph_grid_size(int model, int layout, int prec, int* G, int* wpc) {
 }
 
 cudaError_t graph_init(const CcdParams& P, cudaStream_t s) {
-  k_graph_init<<<1, 32, 0, s>>>(P);
+  k_graph_init<<<dim3(1, P.nfit > 0 ? P.nfit : 1), 32, 0, s>>>(P);
   return cudaGetLastError();
 }
 
@@ -602,19 +652,22 @@ cudaError_t run_ccd_graph(int model, int layout, int prec, const CcdParams& P, c
   // One replay per sweep.  The stop flag of replay i is read while replay
   // i + 1 runs; kernels of a replay after the stop return at once.  The
   // device stops at the evaluation of sweep max_sweeps at the latest, which
-  // falls in replay max_sweeps.
+  // falls in replay max_sweeps.  A batched launch ends when every fit has
+  // counted itself as stopped.
   const int max_replays = P.max_sweeps + 2;
+  const int target = P.nfit > 0 ? P.nfit : 1;
+  const void* stop_src =
+      P.nfit > 0 ? static_cast<const void*>(P.done_count) : static_cast<const void*>(&P.gctl->done);
   int i = 0;
   for (; i < max_replays; ++i) {
     if ((st = cudaGraphLaunch(gc->exec, s)) != cudaSuccess) return st;
     *launches += 2 * P.p;
-    if ((st = cudaMemcpyAsync(gc->flag + (i & 1), &P.gctl->done, sizeof(int), cudaMemcpyDeviceToHost, s)) !=
-        cudaSuccess)
+    if ((st = cudaMemcpyAsync(gc->flag + (i & 1), stop_src, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
       return st;
     if ((st = cudaEventRecord(gc->ev[i & 1], s)) != cudaSuccess) return st;
     if (i >= 1) {
       if ((st = cudaEventSynchronize(gc->ev[(i - 1) & 1])) != cudaSuccess) return st;
-      if (gc->flag[(i - 1) & 1]) {
+      if (gc->flag[(i - 1) & 1] >= target) {
         ++i;
         break;
       }

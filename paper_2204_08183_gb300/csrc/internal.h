@@ -17,6 +17,7 @@ enum : unsigned {
   PREP_STATUS = 2u,
   PREP_NONFINITE = 4u,
   PREP_INDEX = 8u,
+  PREP_FOLD = 16u,
 };
 
 // Parameters of the persistent CCD kernel (passed as a __grid_constant__).
@@ -70,6 +71,18 @@ struct CcdParams {
   uint64_t* wt;          // [M][nwarps] warp totals of the last pass (8-byte payload words)
   uint64_t* agg;         // [kRep][M][G] CTA aggregates of the last pass, replicated
   struct GraphCtl* gctl; // fit state carried between kernels
+  unsigned* done_count;  // fits that have stopped (the host polls it)
+
+  // Batched fits (cross-validation path): fit f = blockIdx.y of every kernel
+  // takes its parameters from fits[f], a complete copy of this struct whose
+  // pointers lead to the fit's own e, eta, beta, width, pen, outputs,
+  // records and control lines, and to its fold's event counts dk and
+  // delta^T X.  Subjects of the fit's fold are held out: their e stays 0.
+  // nfit = 0 and fits = null for one fit.
+  int32_t nfit;
+  int32_t fold;               // the fit's held-out fold (fold_id null: unused)
+  const int8_t* fold_id;      // [n] fold of each subject, or null
+  const struct CcdParams* fits;  // [nfit] per-fit parameters (device memory)
 };
 
 // Fit state of the per-coordinate kernel pair.  The last transform CTA of
@@ -202,6 +215,33 @@ cudaError_t prep_fill_f64(double* v, double value, int64_t count, cudaStream_t s
 cudaError_t prep_convert_dense(const void* src, int src_dtype, int64_t n, int64_t p, void* dst, int prec,
                                int64_t ld, cudaStream_t s);
 cudaError_t prep_convert_vec(const void* src, int src_dtype, int64_t count, void* dst, int prec, cudaStream_t s);
+
+// ---- cross-validated path and lambda_max (cv.cu) -------------------------
+// fold ids outside [0, nfolds) set PREP_FOLD in *perr
+cudaError_t cv_check_folds(const int8_t* fold_id, int64_t n, int nfolds, unsigned* perr, cudaStream_t s);
+// dk [nfolds][K]: events of each group outside each fold; events [nfolds] (zeroed by the caller) += their totals
+cudaError_t cv_fold_stats(const int32_t* gend, int32_t K, const int8_t* status, const int8_t* fold_id, int nfolds,
+                          int32_t* dk, int32_t* events, cudaStream_t s);
+// dTx [nfolds][p]: delta^T X_j over the subjects outside each fold (layout 0 CSC, 1 dense)
+cudaError_t cv_dtx(int layout, int prec, const int64_t* col_ptr, const int32_t* row_idx, const void* values,
+                   int64_t ld, int64_t n, int64_t p, const int8_t* status, const int8_t* fold_id, int nfolds,
+                   double* dTx, cudaStream_t s);
+// e [nfit][n] = 1 outside the fit's fold (f % nfolds), 0 inside; eta [nfit][n] = 0
+cudaError_t cv_init(int prec, int64_t n, const int8_t* fold_id, int nfolds, int nfit, void* e, void* eta,
+                    cudaStream_t s);
+// heldout [nfit]: log partial likelihood of each fit's fold on its own risk
+// sets at eta [nfit][n]; den [nfit][K] scratch
+cudaError_t cv_heldout(int prec, int64_t n, const int32_t* time, const int8_t* status, const int8_t* fold_id,
+                       int nfolds, int nfit, const void* eta, const int32_t* dk_all, const int32_t* dk_fold,
+                       int32_t K, double* den, double* heldout, cudaStream_t s);
+// cv_mean [nlambda] and *best (device)
+cudaError_t cv_select(const double* heldout, int nlambda, int nfolds, double* cv_mean, int32_t* best,
+                      cudaStream_t s);
+// *out (device) = max_j |l'_j(0)| / pf_j for Cox; lam [K], r [n], g [p] scratch
+cudaError_t lambda_max_device(int layout, int prec, const int64_t* col_ptr, const int32_t* row_idx,
+                              const void* values, int64_t ld, int64_t n, int64_t p, const int8_t* status,
+                              const int32_t* gend, const int32_t* dk, int32_t K, const double* pf, double* lam,
+                              double* r, double* g, double* out, cudaStream_t s);
 
 // Text returned by surv_last_error() on the calling thread (api.cu).
 void set_last_error_text(const char* msg);

@@ -58,6 +58,11 @@ int main(void) {
   printf("surv_opts %zu\n", sizeof(surv_opts));
   printf("surv_fit_info %zu\n", sizeof(surv_fit_info));
   printf("surv_nll_data %zu\n", sizeof(surv_nll_data));
+  printf("surv_cv_info %zu\n", sizeof(surv_cv_info));
+  F(surv_cv_info, nfits); F(surv_cv_info, best_lambda); F(surv_cv_info, max_sweeps_used);
+  F(surv_cv_info, fits_converged); F(surv_cv_info, graph_replays); F(surv_cv_info, ctas_per_fit);
+  F(surv_cv_info, kernel_launches); F(surv_cv_info, n_groups); F(surv_cv_info, ccd_kernel_ms);
+  F(surv_cv_info, heldout_ms);
   F(surv_nll_data, n); F(surv_nll_data, p); F(surv_nll_data, ncols); F(surv_nll_data, time);
   F(surv_nll_data, status); F(surv_nll_data, X);
   F(surv_data, n); F(surv_data, p); F(surv_data, time); F(surv_data, status); F(surv_data, layout);
@@ -77,7 +82,8 @@ int main(void) {
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
     c = dict(line.split() for line in out if line.strip())
     structs = {"surv_data": binding.surv_data, "surv_opts": binding.surv_opts,
-               "surv_fit_info": binding.surv_fit_info, "surv_nll_data": binding.surv_nll_data}
+               "surv_fit_info": binding.surv_fit_info, "surv_nll_data": binding.surv_nll_data,
+               "surv_cv_info": binding.surv_cv_info}
     for name, cls in structs.items():
         assert int(c[name]) == C.sizeof(cls), name
     for key, off in c.items():
