@@ -51,9 +51,12 @@ def parse():
     ap.add_argument("--p", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["ccd", "autograd"], default="ccd",
+    ap.add_argument("--workload", choices=["ccd", "autograd", "cv"], default="ccd",
                     help="ccd: the headline penalised Cox fit; autograd: forward + backward of the "
-                         "differentiable Cox NLL at N=2^22, p=256, 64 columns (bf16 X)")
+                         "differentiable Cox NLL at N=2^22, p=256, 64 columns (bf16 X); cv: 10-fold "
+                         "cross-validation x 20 L1 strengths (200 Cox fits) at N=1e6, p=500, 1%% binary")
+    ap.add_argument("--ctas", type=int, default=0, help="cv: CTAs per fit (0 = the library's choice)")
+    ap.add_argument("--no-sequential", action="store_true", help="cv: skip the 200 sequential plain fits")
     ap.add_argument("--schedule", choices=["graph", "persistent"], default="graph",
                     help="graph: two kernels per coordinate replayed as a CUDA graph (default); "
                          "persistent: one cooperative launch per fit")
@@ -408,6 +411,197 @@ def run_autograd(args, rank, world):
     return out
 
 
+# ------------------------------------------ cross-validated path (f1)
+CV_METRIC = "CV fits/s, Cox 10-fold x 20 L1 lambdas (200 fits), N=1e6 p=500 1% binary CSC"
+
+
+def cv_workload():
+    from paper_2204_08183_gb300 import synth
+    d = synth.cohort_cox_sparse(1_000_000, 500, seed=41, density=0.01, n_true=10, laplace_scale=0.2,
+                                censor_frac=0.4, grid=3650)
+    fold = synth.cv_folds(1_000_000, 10, seed=42)
+    return d, fold
+
+
+def run_cv(args, rank, world):
+    """One step = one cox_cv_path call: 10 folds x 20 L1 strengths from
+    lambda_max down to 1e-3 lambda_max, 200 cold-started fits in one batched
+    graph schedule, then the held-out scores and the choice of lambda.
+    Device-resident inputs; e2e = the same call on pinned host arrays.  The
+    same 200 fits as sequential plain cox_fit calls (one per training set,
+    device-resident subsets) are timed once for comparison."""
+    import torch
+    from paper_2204_08183_gb300 import binding, synth
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    d, fold = cv_workload()
+    n, p = d["n"], d["p"]
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    sd = binding.SurvData(dev(d["time"]), dev(d["status"]), col_ptr=dev(d["col_ptr"]), row_idx=dev(d["row_idx"]),
+                          values=dev(d["values"]), n=n, p=p)
+    fold_d = dev(fold)
+    lmax = binding.cox_lambda_max(sd)
+    lam = synth.lambda_grid(lmax, 20)
+    ws = binding.Workspace()
+    stream = torch.cuda.current_stream()
+    kw = dict(penalty="l1", tol=1e-8, max_sweeps=1000, workspace=ws, ctas_per_fit=args.ctas)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(1.5)
+    for w in range(args.warmup):
+        # the first warm-up call tunes the CTAs per fit (kept in the workspace)
+        tune = binding.SURV_FLAG_CV_TUNE if (w == 0 and args.ctas == 0) else 0
+        binding.cox_cv_path(sd, fold_d, 10, lam, flags=tune, **kw)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res = []
+    ev0.record(stream)
+    for _ in range(args.steps):
+        res.append(binding.cox_cv_path(sd, fold_d, 10, lam, **kw))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    t_max = ms
+    if world > 1:
+        tt = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(tt.item())
+    F = 200
+    value = world * F * args.steps / (t_max / 1e3)
+    infos = [r["info"] for r in res]
+    last = res[-1]
+    # roofline of the batched pass: every active fit reads its e over all N
+    # rows and column j's slice per coordinate, plus the eta / e update of
+    # the column's rows after a nonzero step
+    nnz = int(d["col_ptr"][-1])
+    K = infos[-1]["n_groups"]
+    passes = sum(i["coordinate_passes"] for i in infos)
+    upd = sum(i["eta_updates"] for i in infos)
+    per_pass = 4 * n + 8 * nnz / p + 8 * K
+    per_update = 28 * nnz / p
+    alg = passes * per_pass + upd * per_update
+    kern_ms = sum(i["ccd_kernel_ms"] for i in infos)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = alg / (kern_ms / 1e3) / 1e9
+    sweeps = last["sweeps"]
+    out = {"metric": CV_METRIC, "value": round(value, 2), "unit": "fits/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "cox_cv10x20_l1_csc_n1000000_p500", "n": n, "p": p, "density": 0.01,
+                      "folds": 10, "fold_sizes": [int(x) for x in np.bincount(fold, minlength=10)],
+                      "lambdas": 20, "lambda_max": lmax, "lambda_ratio": 1e-3, "tol": 1e-8, "censoring": 0.4,
+                      "time_grid": 3650, "start": "cold (beta = 0) for every fit",
+                      "ctas_per_fit": infos[-1]["ctas_per_fit"],
+                      "ctas_source": "autotuned (one timed sweep per candidate, first warm-up call)"
+                      if args.ctas == 0 else "--ctas",
+                      "l2": "inputs larger than L2 (e + eta of 200 fits: 2.4 GB)"},
+           "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                        "frac": round(achieved / peak, 4), "traffic": None,
+                        "unit_of_work": "one coordinate of one active fit (batched row pass)",
+                        "algorithmic_bytes_per_coordinate": round(alg / max(passes, 1)),
+                        "coordinate_passes_per_step": passes / len(infos),
+                        "eta_updates_per_step": upd / len(infos),
+                        "ccd_ms_per_step": round(kern_ms / len(infos), 3),
+                        "heldout_ms_per_step": round(sum(i["heldout_ms"] for i in infos) / len(infos), 3),
+                        "graph_replays": infos[-1]["graph_replays"],
+                        "kernel": "k_pass + k_trans <cox,csc,f32,batched>, grid (ctas_per_fit, 200)"},
+           "clocks": clk, "gpu_launches": int(sum(i["kernel_launches"] for i in infos)),
+           "cv": {"best_lambda": infos[-1]["best_lambda"], "sweeps_max": int(sweeps.max()),
+                  "sweeps_mean": float(sweeps.mean()), "fits_converged": infos[-1]["fits_converged"],
+                  "cv_mean": [round(float(x), 3) for x in last["cv_mean"]]}}
+    if not args.no_e2e:
+        host = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+        ht, hs, hcp, hri, hv, hf = (host(d["time"]), host(d["status"]), host(d["col_ptr"]), host(d["row_idx"]),
+                                    host(d["values"]), host(fold))
+        hd = binding.SurvData(ht, hs, col_ptr=hcp, row_idx=hri, values=hv, n=n, p=p)
+        binding.cox_cv_path(hd, hf, 10, lam, **kw)
+        torch.cuda.synchronize()
+        e_steps = max(1, min(args.steps, 2))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(e_steps):
+            binding.cox_cv_path(hd, hf, 10, lam, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ems = e0.elapsed_time(e1) / e_steps
+        h2d = sum(int(a.numel() * a.element_size()) for a in (ht, hs, hcp, hri, hv, hf)) + 8 * 20
+        d2h = 8 * F * p + 8 * F + 8 * 20 + 4 * F
+        out["e2e"] = {"value": round(world * F * 1e3 / ems, 2), "unit": "fits/s", "h2d_bytes_per_step": h2d,
+                      "d2h_bytes_per_step": d2h,
+                      "note": "cox_cv_path on pinned host arrays: the library copies them in and the 200 "
+                              "coefficient vectors, scores and sweep counts out inside the call"}
+    if not args.no_sequential and rank == 0:
+        # the same fits one after another through the plain cox_fit (each
+        # training set built once on the device beforehand, untimed)
+        subs = []
+        for k in range(10):
+            m = fold != k
+            rows = np.flatnonzero(m)
+            newidx = np.full(n, -1, np.int64)
+            newidx[rows] = np.arange(rows.shape[0])
+            cp = [0]
+            ri = []
+            for j in range(p):
+                r = d["row_idx"][d["col_ptr"][j]:d["col_ptr"][j + 1]]
+                r = newidx[r]
+                r = r[r >= 0].astype(np.int32)
+                ri.append(r)
+                cp.append(cp[-1] + r.shape[0])
+            ri = np.concatenate(ri)
+            subs.append(binding.SurvData(dev(d["time"][m]), dev(d["status"][m]), col_ptr=dev(np.array(cp, np.int64)),
+                                         row_idx=dev(ri), values=dev(np.ones(ri.shape[0], np.float32)),
+                                         n=int(m.sum()), p=p))
+        ws2 = binding.Workspace()
+        beta = torch.zeros(p, dtype=torch.float64, device="cuda")
+        binding.cox_fit(subs[0], beta=beta, penalty="l1", lam=float(lam[10]), tol=1e-8, max_sweeps=1000,
+                        workspace=ws2)
+        torch.cuda.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for li in range(20):
+            for k in range(10):
+                beta.zero_()
+                binding.cox_fit(subs[k], beta=beta, penalty="l1", lam=float(lam[li]), tol=1e-8, max_sweeps=1000,
+                                workspace=ws2)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        sms = s0.elapsed_time(s1)
+        out["sequential_plain"] = {"value": round(F * 1e3 / sms, 3), "unit": "fits/s", "ms": round(sms, 1),
+                                   "note": "the 200 fits as sequential cox_fit calls on device-resident "
+                                           "training sets (same lambdas, cold start, same tolerance)"}
+        out["speedup_vs_sequential_plain"] = round(value / (F * 1e3 / sms), 2)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import scipy.sparse
+        import oracle
+        m = fold != 0
+        nc = 4
+        cp = d["col_ptr"][: nc + 1]
+        X = scipy.sparse.csc_matrix((np.ones(int(cp[-1])), d["row_idx"][: int(cp[-1])], cp), shape=(n, nc))
+        Xt = X[np.flatnonzero(m)]
+        t0 = time.perf_counter()
+        oracle.ccd_fit("cox", d["time"][m], d["status"][m], Xt, "l1", float(lam[10]), tol=0.0, max_sweeps=1)
+        dt = time.perf_counter() - t0
+        per_pass = dt / (nc + 2)
+        avg_passes = passes / len(infos) / F
+        out["cpu_baseline"] = {"value": round(1.0 / (per_pass * avg_passes), 6), "unit": "fits/s", "cores": 1,
+                               "kind": "oracle",
+                               "sample": "oracle.ccd_fit on fold 0's training set (9e5 subjects), one sweep over "
+                                         "4 columns (%d risk-set passes, %.1f s); fits/s = 1 / (time per pass x "
+                                         "%.0f passes per fit, the GPU run's mean)" % (nc + 2, dt, avg_passes)}
+    return out
+
+
 def run_reference(args, rank, world):
     """The oracle on the host cores: each step one bounded sample."""
     if rank != 0:
@@ -448,6 +642,8 @@ def main():
         out = run_reference(args, rank, world)
     elif args.workload == "autograd":
         out = run_autograd(args, rank, world)
+    elif args.workload == "cv":
+        out = run_cv(args, rank, world)
     else:
         out = run_gpu(args, rank, world)
     if rank == 0 and out is not None:

@@ -123,6 +123,12 @@ typedef struct surv_opts {
  * coordinates; this flag exists to compare them.  loglik_grad_hess always
  * uses the persistent kernel. */
 #define SURV_FLAG_PERSISTENT 2
+/* cox_cv_path only, with ctas_per_fit = 0: time one sweep of the batched
+ * schedule for each of a few CTA-per-fit counts around the default (every
+ * candidate from the same cold start), run the path with the fastest, and
+ * keep that count in the workspace for later calls with the same shape
+ * (n, p, number of fits, layout, precision). */
+#define SURV_FLAG_CV_TUNE 4
 
 /* Fill *opts with defaults: no penalty, FP32-compensated precision,
  * tol 1e-8, max_sweeps 1000, default stream, no workspace. */
@@ -293,6 +299,8 @@ typedef struct surv_cv_info {
   int32_t ctas_per_fit;          /* CTAs each fit runs on in the batched kernels     */
   int64_t kernel_launches;       /* CUDA kernels launched (graph nodes counted)      */
   int64_t n_groups;              /* tie groups K of the whole data                   */
+  int64_t coordinate_passes;     /* risk-set passes summed over fits                 */
+  int64_t eta_updates;           /* nonzero steps summed over fits                   */
   double ccd_kernel_ms;          /* batched CCD: first replay to the last stop       */
   double heldout_ms;             /* held-out scores and the choice of lambda         */
 } surv_cv_info;
@@ -315,9 +323,11 @@ typedef struct surv_cv_info {
  *   0..nfolds-1 of each subject in data order; every fold's training part
  *   needs an event (SURV_E_NO_EVENTS otherwise).  lambdas [nlambda] host
  *   doubles >= 0.  opts: penalty (L1 or L2), precision, tol, max_sweeps,
- *   penalty_factor, stream and workspace as for cox_fit (lambda and flags
- *   are ignored).  ctas_per_fit: CTAs per fit in the batched kernels, or 0
- *   to choose it from the device's SM count and the number of fits.
+ *   penalty_factor, stream and workspace as for cox_fit (lambda is
+ *   ignored; flags may hold SURV_FLAG_CV_TUNE).  ctas_per_fit: CTAs per fit
+ *   in the batched kernels, or 0 for the value tuned earlier on this
+ *   workspace for the same shape, else a default from the device's SM
+ *   count and the number of fits.
  * Outputs (host or device, any may be NULL except beta_out):
  *   beta_out [nlambda][nfolds][p] doubles (fit f = l * nfolds + k),
  *   heldout [nlambda][nfolds], cv_mean [nlambda] doubles,

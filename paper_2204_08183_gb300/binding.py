@@ -38,6 +38,7 @@ SURV_PEN = {"none": 0, "l1": 1, "l2": 2}
 SURV_PREC = {"f32c": 0, "f64": 1}
 SURV_FLAG_TEST_STALL = 1
 SURV_FLAG_PERSISTENT = 2
+SURV_FLAG_CV_TUNE = 4
 
 # exported symbols, in the order the header declares them
 EXPORTS = ["surv_opts_default", "surv_workspace_create", "surv_workspace_destroy", "surv_sort_desc",
@@ -80,8 +81,8 @@ class surv_fit_info(C.Structure):
 class surv_cv_info(C.Structure):
     _fields_ = [("nfits", C.c_int32), ("best_lambda", C.c_int32), ("max_sweeps_used", C.c_int32),
                 ("fits_converged", C.c_int32), ("graph_replays", C.c_int32), ("ctas_per_fit", C.c_int32),
-                ("kernel_launches", C.c_int64), ("n_groups", C.c_int64), ("ccd_kernel_ms", C.c_double),
-                ("heldout_ms", C.c_double)]
+                ("kernel_launches", C.c_int64), ("n_groups", C.c_int64), ("coordinate_passes", C.c_int64),
+                ("eta_updates", C.c_int64), ("ccd_kernel_ms", C.c_double), ("heldout_ms", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -601,17 +601,14 @@ struct CvCtrl {
   int32_t events[128];   // training events per fold
 };
 
-// CTAs per fit when the caller leaves it to the library: the smallest count
-// whose total over all fits fills the co-resident slots to at least 90 %
-// in the last wave, within the rows available.
-int cv_ctas_per_fit(int F, int Gmax, int max_by_rows) {
+// CTAs per fit when neither the caller nor the tuner chose: about ten waves
+// of co-resident CTAs over all fits (measured best at N = 10^6, 200 fits:
+// 16 CTAs per fit; 1 gave 98 fits/s, 3 gave 142, 16 gave 179, 48 gave 147),
+// within the rows available (at least one 32-row word per warp).
+int cv_ctas_default(int F, int Gmax, int max_by_rows) {
   const int lim = std::max(1, std::min(Gmax, max_by_rows));
-  for (int g = 1; g <= lim; ++g) {
-    const int64_t tot = (int64_t)g * F;
-    const int64_t waves = (tot + Gmax - 1) / Gmax;
-    if ((double)tot / (double)(waves * Gmax) >= 0.9) return g;
-  }
-  return lim;
+  const int g = (int)((10LL * Gmax + F / 2) / F);
+  return std::max(1, std::min(g, lim));
 }
 
 int cv_impl(const surv_data* d, const int8_t* fold_id, int nfolds, const double* lambdas, int nlambda,
@@ -630,12 +627,17 @@ int cv_impl(const surv_data* d, const int8_t* fold_id, int nfolds, const double*
   if (ctas_per_fit < 0) { set_error("negative ctas_per_fit"); return SURV_E_INVALID; }
   if (o.penalty < 0 || o.penalty > 2 || o.precision < 0 || o.precision > 1) { set_error("bad penalty/precision"); return SURV_E_INVALID; }
   if (!(o.tol >= 0.0) || o.max_sweeps < 0) { set_error("bad tol/max_sweeps"); return SURV_E_INVALID; }
+  if ((o.flags & ~SURV_FLAG_CV_TUNE) != 0) { set_error("unknown flags for cox_cv_path"); return SURV_E_INVALID; }
   const int64_t n = d->n, p = d->p;
   const int F = nfolds * nlambda;
   const int layout = d->layout;
   const int prec = o.precision;
   const size_t tsz = prec == 0 ? 4 : 8;
   constexpr int M = 3;
+  // per-fit strides: every fit's arrays start on a 256-byte boundary (the
+  // pass reads e with 16-byte vector loads)
+  auto pad = [](size_t elems, size_t esz) { return (elems * esz + 255) / 256 * 256 / esz; };
+  const int64_t fit_n = (int64_t)pad((size_t)n, 8);  // elements of e and eta per fit
   cudaStream_t s = static_cast<cudaStream_t>(o.stream);
   int64_t launches = 0;
   WsGuard guard;
@@ -657,16 +659,27 @@ int cv_impl(const surv_data* d, const int8_t* fold_id, int nfolds, const double*
   for (int64_t j = 0; j < p; ++j)
     if (!std::isfinite(pf_h[j]) || pf_h[j] < 0.0) { set_error("invalid penalty factor at %lld", (long long)j); return SURV_E_NONFINITE; }
 
-  // grid of each fit
+  // CTAs per fit: the caller's, else the tuned value kept in the workspace
+  // for this shape, else the default; SURV_FLAG_CV_TUNE times one sweep for
+  // each candidate first and keeps the fastest
   int Gmax = 0, wpc = 0;
   CUDA_TRY(survgpu::graph_grid_size(SURV_COX, layout, prec, &Gmax, &wpc));
   if (Gmax < 1) { set_error("CCD kernels do not fit on the device"); return SURV_E_CUDA; }
   const int64_t nwords = (n + 31) / 32;
   const int max_by_rows = (int)std::min<int64_t>(Gmax, std::max<int64_t>(1, nwords / wpc));
-  const int G = ctas_per_fit > 0 ? std::min(ctas_per_fit, Gmax) : cv_ctas_per_fit(F, Gmax, max_by_rows);
-  const int32_t nwarps = G * wpc;
-  const int32_t wpw = (int32_t)((nwords + nwarps - 1) / nwarps);
-  const int64_t rows_per_warp = (int64_t)wpw * 32;
+  const bool tune = ctas_per_fit == 0 && (o.flags & SURV_FLAG_CV_TUNE) != 0;
+  const int64_t tkey[6] = {n, p, (int64_t)F, (int64_t)layout * 2 + prec, (int64_t)d->dtype,
+                           d->layout == SURV_CSC ? (int64_t)-1 : (int64_t)0};
+  int G = ctas_per_fit > 0 ? std::min(ctas_per_fit, Gmax) : cv_ctas_default(F, Gmax, max_by_rows);
+  if (ctas_per_fit == 0 && !tune && ws->cv_tuned_ctas > 0 && std::memcmp(ws->cv_tune_key, tkey, sizeof(tkey)) == 0)
+    G = ws->cv_tuned_ctas;
+  std::vector<int> cands;
+  if (tune) {
+    for (int g : {G / 2, G, 2 * G, 3 * G})
+      if (g >= 1 && g <= max_by_rows && std::find(cands.begin(), cands.end(), g) == cands.end()) cands.push_back(g);
+    if (cands.empty()) cands.push_back(G);
+  }
+  const int Galloc = tune ? *std::max_element(cands.begin(), cands.end()) : G;
 
   // staging and validation
   Staged stg;
@@ -681,23 +694,27 @@ int cv_impl(const surv_data* d, const int8_t* fold_id, int nfolds, const double*
   if ((rc = device_view(ws, W::CV_FOLD, fold_id, (size_t)n, s, &fold_v))) return rc;
   const int8_t* fold_d = static_cast<const int8_t*>(fold_v);
 
-  // shared tables, per-fold tables, per-fit state
+  // shared tables, per-fold tables, per-fit state (scratch sized for the
+  // largest grid tried)
+  const int32_t nwarps_alloc = Galloc * wpc;
   void *gend, *dk, *ck, *wk0, *woff = nullptr, *dkf, *dtxf, *cvc_v;
   void *e, *eta, *rec, *wt, *agg, *part, *gctl, *beta, *width, *pen, *out, *fits, *den, *held, *mean;
+  const size_t rec_f = pad((size_t)K * M, 8), wt_f = pad((size_t)M * nwarps_alloc, 8);
+  const size_t agg_f = pad((size_t)survgpu::kRep * M * Galloc, 8), part_f = pad((size_t)3 * Galloc, 8);
   if ((rc = ensure(ws, W::GEND, 4 * (size_t)K, &gend))) return rc;
   if ((rc = ensure(ws, W::DK, 4 * (size_t)K, &dk))) return rc;
   if ((rc = ensure(ws, W::CK, 4 * (size_t)K, &ck))) return rc;
-  if ((rc = ensure(ws, W::WK0, 4 * (size_t)(nwarps + 1), &wk0))) return rc;
-  if (layout == SURV_CSC && (rc = ensure(ws, W::WOFF, 4 * (size_t)p * (nwarps + 1), &woff))) return rc;
+  if ((rc = ensure(ws, W::WK0, 4 * (size_t)(nwarps_alloc + 1), &wk0))) return rc;
+  if (layout == SURV_CSC && (rc = ensure(ws, W::WOFF, 4 * (size_t)p * (nwarps_alloc + 1), &woff))) return rc;
   if ((rc = ensure(ws, W::CV_DK, 4 * (size_t)nfolds * K, &dkf))) return rc;
   if ((rc = ensure(ws, W::CV_DTX, 8 * (size_t)nfolds * p, &dtxf))) return rc;
   if ((rc = ensure(ws, W::CV_CTRL, sizeof(CvCtrl), &cvc_v))) return rc;
-  if ((rc = ensure(ws, W::CV_E, tsz * (size_t)F * n, &e))) return rc;
-  if ((rc = ensure(ws, W::CV_ETA, 8 * (size_t)F * n, &eta))) return rc;
-  if ((rc = ensure(ws, W::CV_REC, 8 * (size_t)F * K * M, &rec))) return rc;
-  if ((rc = ensure(ws, W::CV_WT, 8 * (size_t)F * M * nwarps, &wt))) return rc;
-  if ((rc = ensure(ws, W::CV_AGG, 8 * (size_t)F * survgpu::kRep * M * G, &agg))) return rc;
-  if ((rc = ensure(ws, W::CV_PART, 8 * (size_t)F * 3 * G, &part))) return rc;
+  if ((rc = ensure(ws, W::CV_E, tsz * (size_t)F * fit_n, &e))) return rc;
+  if ((rc = ensure(ws, W::CV_ETA, 8 * (size_t)F * fit_n, &eta))) return rc;
+  if ((rc = ensure(ws, W::CV_REC, 8 * (size_t)F * rec_f, &rec))) return rc;
+  if ((rc = ensure(ws, W::CV_WT, 8 * (size_t)F * wt_f, &wt))) return rc;
+  if ((rc = ensure(ws, W::CV_AGG, 8 * (size_t)F * agg_f, &agg))) return rc;
+  if ((rc = ensure(ws, W::CV_PART, 8 * (size_t)F * part_f, &part))) return rc;
   if ((rc = ensure(ws, W::CV_GCTL, sizeof(survgpu::GraphCtl) * (size_t)F, &gctl))) return rc;
   if ((rc = ensure(ws, W::CV_BETA, 8 * (size_t)F * p, &beta))) return rc;
   if ((rc = ensure(ws, W::CV_WIDTH, 8 * (size_t)F * p, &width))) return rc;
@@ -718,24 +735,11 @@ int cv_impl(const surv_data* d, const int8_t* fold_id, int nfolds, const double*
                                   static_cast<int32_t*>(dkf), cvc->events, s));
   CUDA_TRY(survgpu::cv_dtx(layout == SURV_CSC ? 0 : 1, prec, stg.colptr, stg.rowidx, stg.vals, stg.ld, n, p,
                            stg.status, fold_d, nfolds, static_cast<double*>(dtxf), s));
-  if (layout == SURV_CSC) {
-    CUDA_TRY(survgpu::prep_warp_offsets(stg.colptr, stg.rowidx, p, n, nwarps, rows_per_warp,
-                                        static_cast<int32_t*>(woff), s));
-    ++launches;
-  }
-  CUDA_TRY(survgpu::prep_warp_groups(static_cast<int32_t*>(gend), K, n, nwarps, rows_per_warp,
-                                     static_cast<int32_t*>(wk0), s));
-  CUDA_TRY(survgpu::cv_init(prec, n, fold_d, nfolds, F, e, eta, s));
-  launches += 7;
+  launches += 5;
   std::vector<double> pen_h((size_t)F * p);
   for (int f = 0; f < F; ++f)
     for (int64_t j = 0; j < p; ++j) pen_h[(size_t)f * p + j] = lam_h[f / nfolds] * pf_h[j];
   CUDA_TRY(cudaMemcpyAsync(pen, pen_h.data(), 8 * pen_h.size(), cudaMemcpyHostToDevice, s));
-  CUDA_TRY(cudaMemsetAsync(beta, 0, 8 * (size_t)F * p, s));
-  CUDA_TRY(survgpu::prep_fill_f64(static_cast<double*>(width), 1.0, (int64_t)F * p, s));
-  CUDA_TRY(cudaMemsetAsync(gctl, 0, sizeof(survgpu::GraphCtl) * (size_t)F, s));
-  CUDA_TRY(cudaMemsetAsync(out, 0, 8 * (size_t)F * survgpu::OUT_COUNT, s));
-  ++launches;
   CvCtrl hcv;
   DevCtrl hc;
   CUDA_TRY(cudaMemcpyAsync(&hcv, cvc, sizeof(CvCtrl), cudaMemcpyDeviceToHost, s));
@@ -746,56 +750,101 @@ int cv_impl(const surv_data* d, const int8_t* fold_id, int nfolds, const double*
   for (int k = 0; k < nfolds; ++k)
     if (hcv.events[k] <= 0) { set_error("no events outside fold %d", k); return SURV_E_NO_EVENTS; }
 
-  // per-fit parameters
-  CcdParams P;
-  std::memset(&P, 0, sizeof(P));
-  P.n = n;
-  P.ld = stg.ld;
-  P.p = (int32_t)p;
-  P.K = K;
-  P.G = G;
-  P.wpc = wpc;
-  P.wpw = wpw;
-  P.nwarps = nwarps;
-  P.gend = static_cast<const int32_t*>(gend);
-  P.wk0 = static_cast<const int32_t*>(wk0);
-  P.col_ptr = stg.colptr;
-  P.row_idx = stg.rowidx;
-  P.values = layout == SURV_CSC ? stg.vals : nullptr;
-  P.woff = static_cast<const int32_t*>(woff);
-  P.X = layout == SURV_DENSE ? stg.vals : nullptr;
-  P.penalty = o.penalty;
-  P.max_sweeps = o.max_sweeps;
-  P.tol = o.tol;
-  P.single_j = -1;
-  P.withhold_cta = -1;
-  P.done_count = &cvc->done;
-  P.nfit = F;
-  P.fold_id = fold_d;
+  // Grid tables, per-fit parameters and a cold start for G CTAs per fit;
+  // *P0 receives the launch parameters (fit 0's, with the table of all fits).
   std::vector<CcdParams> fits_h(F);
-  for (int f = 0; f < F; ++f) {
-    const int k = f % nfolds;
-    CcdParams& Q = fits_h[f];
-    Q = P;
-    Q.fold = k;
-    Q.dk = static_cast<const int32_t*>(dkf) + (size_t)k * K;
-    Q.dTx = static_cast<const double*>(dtxf) + (size_t)k * p;
-    Q.e = static_cast<char*>(e) + tsz * (size_t)f * n;
-    Q.eta = static_cast<char*>(eta) + 8 * (size_t)f * n;
-    Q.rec = static_cast<char*>(rec) + 8 * (size_t)f * K * M;
-    Q.wt = static_cast<uint64_t*>(wt) + (size_t)f * M * nwarps;
-    Q.agg = static_cast<uint64_t*>(agg) + (size_t)f * survgpu::kRep * M * G;
-    Q.slot_part = reinterpret_cast<unsigned*>(static_cast<uint64_t*>(part) + (size_t)f * 3 * G);
-    Q.gctl = static_cast<survgpu::GraphCtl*>(gctl) + f;
-    Q.beta = static_cast<double*>(beta) + (size_t)f * p;
-    Q.width = static_cast<double*>(width) + (size_t)f * p;
-    Q.pen = static_cast<const double*>(pen) + (size_t)f * p;
-    Q.out = static_cast<double*>(out) + (size_t)f * survgpu::OUT_COUNT;
-    Q.fits = nullptr;
+  auto setup = [&](int Gc, CcdParams* P0) -> int {
+    const int32_t nwarps = Gc * wpc;
+    const int32_t wpw = (int32_t)((nwords + nwarps - 1) / nwarps);
+    const int64_t rows_per_warp = (int64_t)wpw * 32;
+    if (layout == SURV_CSC) {
+      CUDA_TRY(survgpu::prep_warp_offsets(stg.colptr, stg.rowidx, p, n, nwarps, rows_per_warp,
+                                          static_cast<int32_t*>(woff), s));
+      ++launches;
+    }
+    CUDA_TRY(survgpu::prep_warp_groups(static_cast<int32_t*>(gend), K, n, nwarps, rows_per_warp,
+                                       static_cast<int32_t*>(wk0), s));
+    CUDA_TRY(survgpu::cv_init(prec, n, fit_n, fold_d, nfolds, F, e, eta, s));
+    CUDA_TRY(survgpu::prep_fill_f64(static_cast<double*>(width), 1.0, (int64_t)F * p, s));
+    launches += 3;
+    CUDA_TRY(cudaMemsetAsync(beta, 0, 8 * (size_t)F * p, s));
+    CUDA_TRY(cudaMemsetAsync(gctl, 0, sizeof(survgpu::GraphCtl) * (size_t)F, s));
+    CUDA_TRY(cudaMemsetAsync(out, 0, 8 * (size_t)F * survgpu::OUT_COUNT, s));
+    CUDA_TRY(cudaMemsetAsync(&cvc->done, 0, sizeof(unsigned), s));
+    CcdParams P;
+    std::memset(&P, 0, sizeof(P));
+    P.n = n;
+    P.ld = stg.ld;
+    P.p = (int32_t)p;
+    P.K = K;
+    P.G = Gc;
+    P.wpc = wpc;
+    P.wpw = wpw;
+    P.nwarps = nwarps;
+    P.gend = static_cast<const int32_t*>(gend);
+    P.wk0 = static_cast<const int32_t*>(wk0);
+    P.col_ptr = stg.colptr;
+    P.row_idx = stg.rowidx;
+    P.values = layout == SURV_CSC ? stg.vals : nullptr;
+    P.woff = static_cast<const int32_t*>(woff);
+    P.X = layout == SURV_DENSE ? stg.vals : nullptr;
+    P.penalty = o.penalty;
+    P.max_sweeps = o.max_sweeps;
+    P.tol = o.tol;
+    P.single_j = -1;
+    P.withhold_cta = -1;
+    P.done_count = &cvc->done;
+    P.nfit = F;
+    P.fold_id = fold_d;
+    for (int f = 0; f < F; ++f) {
+      const int k = f % nfolds;
+      CcdParams& Q = fits_h[f];
+      Q = P;
+      Q.fold = k;
+      Q.dk = static_cast<const int32_t*>(dkf) + (size_t)k * K;
+      Q.dTx = static_cast<const double*>(dtxf) + (size_t)k * p;
+      Q.e = static_cast<char*>(e) + tsz * (size_t)f * fit_n;
+      Q.eta = static_cast<char*>(eta) + 8 * (size_t)f * fit_n;
+      Q.rec = static_cast<char*>(rec) + 8 * (size_t)f * rec_f;
+      Q.wt = static_cast<uint64_t*>(wt) + (size_t)f * wt_f;
+      Q.agg = static_cast<uint64_t*>(agg) + (size_t)f * agg_f;
+      Q.slot_part = reinterpret_cast<unsigned*>(static_cast<uint64_t*>(part) + (size_t)f * part_f);
+      Q.gctl = static_cast<survgpu::GraphCtl*>(gctl) + f;
+      Q.beta = static_cast<double*>(beta) + (size_t)f * p;
+      Q.width = static_cast<double*>(width) + (size_t)f * p;
+      Q.pen = static_cast<const double*>(pen) + (size_t)f * p;
+      Q.out = static_cast<double*>(out) + (size_t)f * survgpu::OUT_COUNT;
+      Q.fits = nullptr;
+    }
+    CUDA_TRY(cudaMemcpyAsync(fits, fits_h.data(), sizeof(CcdParams) * (size_t)F, cudaMemcpyHostToDevice, s));
+    *P0 = fits_h[0];
+    P0->fits = static_cast<const CcdParams*>(fits);
+    CUDA_TRY(survgpu::graph_init(*P0, s));
+    ++launches;
+    return SURV_OK;
+  };
+
+  const int lmode = layout == SURV_CSC ? 0 : 1;
+  CcdParams P0;
+  if (tune) {
+    // one full sweep of every candidate from the same cold start
+    float best_ms = 0.f;
+    int best_g = G;
+    for (int g : cands) {
+      if ((rc = setup(g, &P0))) return rc;
+      float ms = 0.f;
+      CUDA_TRY(survgpu::time_one_sweep(SURV_COX, lmode, prec, P0, s, &ms));
+      launches += 2 * p;
+      if (best_ms == 0.f || ms < best_ms) {
+        best_ms = ms;
+        best_g = g;
+      }
+    }
+    G = best_g;
+    ws->cv_tuned_ctas = G;
+    std::memcpy(ws->cv_tune_key, tkey, sizeof(tkey));
   }
-  CUDA_TRY(cudaMemcpyAsync(fits, fits_h.data(), sizeof(CcdParams) * (size_t)F, cudaMemcpyHostToDevice, s));
-  CcdParams P0 = fits_h[0];
-  P0.fits = static_cast<const CcdParams*>(fits);
+  if ((rc = setup(G, &P0))) return rc;
 
   struct Events {
     cudaEvent_t a = nullptr, b = nullptr, c = nullptr;
@@ -809,15 +858,13 @@ int cv_impl(const surv_data* d, const int8_t* fold_id, int nfolds, const double*
   CUDA_TRY(cudaEventCreate(&ev.b));
   CUDA_TRY(cudaEventCreate(&ev.c));
   int replays = 0, glaunches = 0;
-  CUDA_TRY(survgpu::graph_init(P0, s));
-  ++launches;
-  CUDA_TRY(survgpu::run_ccd_graph(SURV_COX, layout == SURV_CSC ? 0 : 1, prec, P0, s,
-                                  o_in && o_in->workspace ? &ws->graph : nullptr, ev.a, &replays, &glaunches));
+  CUDA_TRY(survgpu::run_ccd_graph(SURV_COX, lmode, prec, P0, s, o_in && o_in->workspace ? &ws->graph : nullptr,
+                                  ev.a, &replays, &glaunches));
   launches += glaunches;
   CUDA_TRY(cudaEventRecord(ev.b, s));
-  CUDA_TRY(survgpu::cv_heldout(prec, n, stg.time, stg.status, fold_d, nfolds, F, eta, static_cast<const int32_t*>(dk),
-                               static_cast<const int32_t*>(dkf), K, static_cast<double*>(den),
-                               static_cast<double*>(held), s));
+  CUDA_TRY(survgpu::cv_heldout(prec, n, fit_n, stg.time, stg.status, fold_d, nfolds, F, eta,
+                               static_cast<const int32_t*>(dk), static_cast<const int32_t*>(dkf), K,
+                               static_cast<double*>(den), static_cast<double*>(held), s));
   CUDA_TRY(survgpu::cv_select(static_cast<const double*>(held), nlambda, nfolds, static_cast<double*>(mean),
                               &cvc->best, s));
   launches += 2;
@@ -835,10 +882,14 @@ int cv_impl(const surv_data* d, const int8_t* fold_id, int nfolds, const double*
   if (cv_mean_out) CUDA_TRY(cudaMemcpyAsync(cv_mean_out, mean, 8 * (size_t)nlambda, cudaMemcpyDefault, s));
   std::vector<int32_t> sw((size_t)F);
   int conv = 0, maxsw = 0;
+  int64_t passes = 0, updates = 0;
   for (int f = 0; f < F; ++f) {
-    sw[f] = (int32_t)out_h[(size_t)f * survgpu::OUT_COUNT + survgpu::OUT_SWEEPS];
-    conv += out_h[(size_t)f * survgpu::OUT_COUNT + survgpu::OUT_CONVERGED] != 0.0;
+    const double* of = out_h.data() + (size_t)f * survgpu::OUT_COUNT;
+    sw[f] = (int32_t)of[survgpu::OUT_SWEEPS];
+    conv += of[survgpu::OUT_CONVERGED] != 0.0;
     maxsw = std::max(maxsw, sw[f]);
+    passes += (int64_t)of[survgpu::OUT_PASSES];
+    updates += (int64_t)of[survgpu::OUT_ETA_UPDATES];
   }
   if (sweeps_out) CUDA_TRY(cudaMemcpyAsync(sweeps_out, sw.data(), 4 * (size_t)F, cudaMemcpyDefault, s));
   CUDA_TRY(cudaStreamSynchronize(s));
@@ -852,6 +903,8 @@ int cv_impl(const surv_data* d, const int8_t* fold_id, int nfolds, const double*
     info->ctas_per_fit = G;
     info->kernel_launches = launches;
     info->n_groups = K;
+    info->coordinate_passes = passes;
+    info->eta_updates = updates;
     float ms = 0.f;
     CUDA_TRY(cudaEventElapsedTime(&ms, ev.a, ev.b));
     info->ccd_kernel_ms = ms;

@@ -178,6 +178,15 @@ struct EndCursor {
     }
     return (int64_t)__shfl_sync(0xffffffffu, reg, kn - base);
   }
+  // after pos(): is the end after the current one also before `limit`?
+  // (true when it lies outside the loaded window: the caller then takes its
+  // general path, which is correct for any number of ends)
+  __device__ __forceinline__ bool second_before(int64_t limit) const {
+    const int k2 = kn + 1;
+    if (k2 >= k_hi) return false;
+    if (k2 - base >= 32) return true;
+    return (int64_t)__shfl_sync(0xffffffffu, reg, k2 - base) < limit;
+  }
 };
 
 // Step 2 for one warp: the tuple sums over rows [row_lo, row_hi) of column j.
@@ -186,7 +195,7 @@ struct EndCursor {
 // the warp totals (every lane holds them).  The dense components stream e
 // (and X, W) in tiles of 32 * U * VEC rows; the CSC components walk the
 // column's nonzeros in the warp's rows (woff holds the per-warp offsets).
-template <int MODEL, int LAYOUT, typename T, int U_, int SR>
+template <int MODEL, int LAYOUT, typename T, int U_, int SR, bool MULTI = false>
 __device__ __forceinline__ void warp_pass(const CcdParams& P, int j, int64_t row_lo, int64_t row_hi,
                                           typename AccOf<T>::type* rec,
                                           typename AccOf<T>::type (&tot)[Cfg<MODEL, LAYOUT, T>::M],
@@ -234,53 +243,107 @@ __device__ __forceinline__ void warp_pass(const CcdParams& P, int j, int64_t row
         }
       }
     };
-    // one tile: warp-relative prefix at each group end inside it, then the
-    // tile sums (pairwise within the lane) into the running sums
+    // One tile.  Lane l holds chunks c = 32 u + l of VEC consecutive rows
+    // (rows t0 + VEC c .. + VEC - 1); chunk sums are pairwise within the
+    // lane and feed the running sums.
+    //   One dense component (CSC layouts of Cox): the lane's share of the
+    //   rows up to an end in chunk c* is its chunks before c* plus chunk c*
+    //   up to the end.  A tile with one end reduces (running sum + share)
+    //   in one float-float tree; a tile with several reduces the running
+    //   sums once and each end's shares in an FP32 tree.
+    //   Several components (register pressure): every end reduces the
+    //   running sums plus the tile's rows up to the end in one tree.
+    auto chunk_sum = [&](int d, const T (&ev)[U][VEC], const T (&xv)[U][VEC], const T (&wv)[U][VEC], int u) {
+      const T a0 = dense_comp<MODEL, LAYOUT, T>(d, ev[u][0], xv[u][0], wv[u][0]);
+      const T a1 = dense_comp<MODEL, LAYOUT, T>(d, ev[u][1], xv[u][1], wv[u][1]);
+      if (VEC == 4) {
+        const T a2 = dense_comp<MODEL, LAYOUT, T>(d, ev[u][VEC > 2 ? 2 : 0], xv[u][VEC > 2 ? 2 : 0],
+                                                  wv[u][VEC > 2 ? 2 : 0]);
+        const T a3 = dense_comp<MODEL, LAYOUT, T>(d, ev[u][VEC > 3 ? 3 : 0], xv[u][VEC > 3 ? 3 : 0],
+                                                  wv[u][VEC > 3 ? 3 : 0]);
+        return (a0 + a1) + (a2 + a3);
+      }
+      return a0 + a1;
+    };
     auto tile = [&](int64_t t0, const T (&ev)[U][VEC], const T (&xv)[U][VEC], const T (&wv)[U][VEC]) {
       const int64_t t_end = min(t0 + (int64_t)TILE, row_hi);
-      while (next_end < t_end) {
-        A pref[ND];
-#pragma unroll
-        for (int d = 0; d < ND; ++d) {
-          T part = T(0);
-#pragma unroll
-          for (int u = 0; u < U; ++u)
-#pragma unroll
-            for (int q = 0; q < VEC; ++q) {
-              const int64_t r = t0 + (int64_t)(lane + 32 * u) * VEC + q;
-              if (r <= next_end) part += dense_comp<MODEL, LAYOUT, T>(d, ev[u][q], xv[u][q], wv[u][q]);
-            }
-          pref[d] = acc_add_v(acc[d], part);
-        }
-        warp_sum_some<ND>(pref);
-        if (lane == 0)
-#pragma unroll
-          for (int d = 0; d < ND; ++d) rec[(size_t)ec.kn * M + C::dmap(d)] = pref[d];
-        ++ec.kn;
-        next_end = ec.pos(P.gend);
-      }
-#pragma unroll
-      for (int d = 0; d < ND; ++d) {
+      if constexpr (ND == 1 && MULTI) {
         T su[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          T a0 = dense_comp<MODEL, LAYOUT, T>(d, ev[u][0], xv[u][0], wv[u][0]);
-          T a1 = dense_comp<MODEL, LAYOUT, T>(d, ev[u][1], xv[u][1], wv[u][1]);
-          if (VEC == 4) {
-            T a2 = dense_comp<MODEL, LAYOUT, T>(d, ev[u][VEC > 2 ? 2 : 0], xv[u][VEC > 2 ? 2 : 0],
-                                                wv[u][VEC > 2 ? 2 : 0]);
-            T a3 = dense_comp<MODEL, LAYOUT, T>(d, ev[u][VEC > 3 ? 3 : 0], xv[u][VEC > 3 ? 3 : 0],
-                                                wv[u][VEC > 3 ? 3 : 0]);
-            su[u] = (a0 + a1) + (a2 + a3);
+        for (int u = 0; u < U; ++u) su[u] = chunk_sum(0, ev, xv, wv, u);
+        auto share = [&](int64_t end) {
+          const int off = (int)(end - t0);
+          const int cstar = off / VEC, qstar = off - cstar * VEC;
+          T part = T(0);
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int c = 32 * u + lane;
+            if (c < cstar) {
+              part += su[u];
+            } else if (c == cstar) {
+#pragma unroll
+              for (int q = 0; q < VEC; ++q)
+                if (q <= qstar) part += dense_comp<MODEL, LAYOUT, T>(0, ev[u][q], xv[u][q], wv[u][q]);
+            }
+          }
+          return part;
+        };
+        if (next_end < t_end) {
+          if (!ec.second_before(t_end)) {
+            A pref[1] = {acc_add_v(acc[0], share(next_end))};
+            warp_sum_some<1>(pref);
+            if (lane == 0) rec[(size_t)ec.kn * M + C::dmap(0)] = pref[0];
+            ++ec.kn;
+            next_end = ec.pos(P.gend);
           } else {
-            su[u] = a0 + a1;
+            A base[1] = {acc[0]};
+            warp_sum_some<1>(base);
+            do {
+              const A pref = acc_add_v(base[0], warp_sum_t(share(next_end)));
+              if (lane == 0) rec[(size_t)ec.kn * M + C::dmap(0)] = pref;
+              ++ec.kn;
+              next_end = ec.pos(P.gend);
+            } while (next_end < t_end);
           }
         }
 #pragma unroll
         for (int s = 1; s < U; s <<= 1)
 #pragma unroll
           for (int u = 0; u + s < U; u += 2 * s) su[u] += su[u + s];
-        acc[d] = acc_add_v(acc[d], su[0]);
+        acc[0] = acc_add_v(acc[0], su[0]);
+      } else {
+        while (next_end < t_end) {
+          A pref[ND];
+#pragma unroll
+          for (int d = 0; d < ND; ++d) {
+            T part = T(0);
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+              for (int q = 0; q < VEC; ++q) {
+                const int64_t r = t0 + (int64_t)(lane + 32 * u) * VEC + q;
+                if (r <= next_end) part += dense_comp<MODEL, LAYOUT, T>(d, ev[u][q], xv[u][q], wv[u][q]);
+              }
+            pref[d] = acc_add_v(acc[d], part);
+          }
+          warp_sum_some<ND>(pref);
+          if (lane == 0)
+#pragma unroll
+            for (int d = 0; d < ND; ++d) rec[(size_t)ec.kn * M + C::dmap(d)] = pref[d];
+          ++ec.kn;
+          next_end = ec.pos(P.gend);
+        }
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+          T su[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) su[u] = chunk_sum(d, ev, xv, wv, u);
+#pragma unroll
+          for (int s = 1; s < U; s <<= 1)
+#pragma unroll
+            for (int u = 0; u + s < U; u += 2 * s) su[u] += su[u + s];
+          acc[d] = acc_add_v(acc[d], su[0]);
+        }
       }
     };
 
@@ -294,66 +357,201 @@ __device__ __forceinline__ void warp_pass(const CcdParams& P, int j, int64_t row
   }
   if (LAYOUT == 0 && NS > 0) {
     // sparse part: the nonzeros of column j inside the warp's rows
-    const int sa = pf.sa, sb = pf.sb;
-    const int32_t* ri = pf.ri;
-    const T* vals = pf.vals;
-    A sacc[NS > 0 ? NS : 1];
+    if constexpr (MULTI) {
+      const int sa = pf.sa, sb = pf.sb;
+      const int32_t* ri = pf.ri;
+      const T* vals = pf.vals;
+      // Two running sums: sacc holds lane partials (plain adds), run the
+      // warp-uniform sum folded in from sacc by rounds with several ends.  A
+      // round with one end reduces sacc plus the round's nonzeros up to the
+      // end in one tree.  A round with several ends folds sacc into run, takes
+      // one inclusive lane scan, and each end reads the scan at the last
+      // nonzero at or before it (row indices increase with the lane, so a
+      // ballot counts them).
+      constexpr int NSX = NS > 0 ? NS : 1;
+      A sacc[NSX], run[NSX];
 #pragma unroll
-    for (int s = 0; s < NS; ++s) acc_zero(sacc[s]);
-    EndCursor ec{pf.k_lo, pf.k_hi, pf.k_lo, pf.kreg};
-    int64_t next_end = ec.pos(P.gend);
-    auto round = [&](int row, T x, T ev, T wv, int nvalid) {
-      T sv[NS > 0 ? NS : 1];
-      sv[0] = ev * x;
-      if (NS > 1) sv[NS > 1 ? 1 : 0] = sv[0] * x;
-      if (NS > 2) {
-        sv[NS > 2 ? 2 : 0] = wv * sv[0];
-        sv[NS > 3 ? 3 : 0] = wv * sv[NS > 1 ? 1 : 0];
+      for (int s = 0; s < NS; ++s) {
+        acc_zero(sacc[s]);
+        acc_zero(run[s]);
       }
-      const int last_row = __shfl_sync(0xffffffffu, row, nvalid - 1);
-      // ends before the round's last nonzero see only part of the round
-      while (next_end < (int64_t)last_row) {
-        A pref[NS > 0 ? NS : 1];
+      bool sacc_dirty = false;
+      EndCursor ec{pf.k_lo, pf.k_hi, pf.k_lo, pf.kreg};
+      int64_t next_end = ec.pos(P.gend);
+      auto round = [&](int row, T x, T ev, T wv, int nvalid) {
+        T sv[NSX];
+        sv[0] = ev * x;
+        if (NS > 1) sv[NS > 1 ? 1 : 0] = sv[0] * x;
+        if (NS > 2) {
+          sv[NS > 2 ? 2 : 0] = wv * sv[0];
+          sv[NS > 3 ? 3 : 0] = wv * sv[NS > 1 ? 1 : 0];
+        }
+        const int last_row = __shfl_sync(0xffffffffu, row, nvalid - 1);
+        if (next_end < (int64_t)last_row && !ec.second_before(last_row)) {
+          // one end in the round: one tree of the lane partials and the
+          // round's nonzeros up to the end
+          A pref[NSX];
 #pragma unroll
-        for (int s = 0; s < NS; ++s) pref[s] = acc_add_v(sacc[s], (int64_t)row <= next_end ? sv[s] : T(0));
-        warp_sum_some<(NS > 0 ? NS : 1)>(pref);
+          for (int s = 0; s < NS; ++s) pref[s] = acc_add_v(sacc[s], (int64_t)row <= next_end ? sv[s] : T(0));
+          warp_sum_some<NSX>(pref);
+          if (lane == 0)
+#pragma unroll
+            for (int s = 0; s < NS; ++s) rec[(size_t)ec.kn * M + C::smap(s)] = acc_add(run[s], pref[s]);
+          ++ec.kn;
+          next_end = ec.pos(P.gend);
+#pragma unroll
+          for (int s = 0; s < NS; ++s) sacc[s] = acc_add_v(sacc[s], sv[s]);
+          sacc_dirty = true;
+        } else if (next_end < (int64_t)last_row) {
+          if (sacc_dirty) {
+            warp_sum_some<NSX>(sacc);
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+              run[s] = acc_add(run[s], sacc[s]);
+              acc_zero(sacc[s]);
+            }
+            sacc_dirty = false;
+          }
+          A sc[NSX];
+#pragma unroll
+          for (int s = 0; s < NS; ++s) {
+            acc_zero(sc[s]);
+            sc[s] = acc_add_v(sc[s], sv[s]);
+          }
+          warp_scan_n<NSX>(sc, lane);
+          while (next_end < (int64_t)last_row) {
+            const int cnt = __popc(__ballot_sync(0xffffffffu, (int64_t)row <= next_end));
+            A pref[NSX];
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+              const A v = shfl_idx(sc[s], cnt > 0 ? cnt - 1 : 0);
+              pref[s] = cnt > 0 ? acc_add(run[s], v) : run[s];
+            }
+            if (lane == 0)
+#pragma unroll
+              for (int s = 0; s < NS; ++s) rec[(size_t)ec.kn * M + C::smap(s)] = pref[s];
+            ++ec.kn;
+            next_end = ec.pos(P.gend);
+          }
+#pragma unroll
+          for (int s = 0; s < NS; ++s) run[s] = acc_add(run[s], shfl_idx(sc[s], 31));
+        } else {
+#pragma unroll
+          for (int s = 0; s < NS; ++s) sacc[s] = acc_add_v(sacc[s], sv[s]);
+          sacc_dirty = true;
+        }
+      };
+      // e (and W) at the prefetched rows
+      T pe[SR], pw[SR];
+#pragma unroll
+      for (int r = 0; r < SR; ++r) {
+        const int row = pf.prow[r];
+        pe[r] = row == INT_MAX ? T(0) : ld_hint(e + row, keep);
+        pw[r] = (MODEL == 1 && row != INT_MAX) ? ld_hint(w2 + row, keep) : T(0);
+      }
+      // one call site of round() (it is large): the first SR rounds take the
+      // prefetched values through a select chain, later rounds load theirs
+      int r = 0;
+      for (int base = sa; base < sb; base += 32, ++r) {
+        int row;
+        T x, ev, wv;
+        if (r < SR) {
+          row = pf.prow[0];
+          x = pf.pval[0];
+          ev = pe[0];
+          wv = pw[0];
+#pragma unroll
+          for (int q = 1; q < SR; ++q)
+            if (r == q) {
+              row = pf.prow[q];
+              x = pf.pval[q];
+              ev = pe[q];
+              wv = pw[q];
+            }
+        } else {
+          const int i = base + lane;
+          const bool valid = i < sb;
+          row = valid ? ld_hint(ri + i, strm) : INT_MAX;
+          x = valid ? (vals ? ld_stream(vals + i, strm) : T(1)) : T(0);
+          ev = valid ? ld_hint(e + row, keep) : T(0);
+          wv = (MODEL == 1 && valid) ? ld_hint(w2 + row, keep) : T(0);
+        }
+        round(row, x, ev, wv, min(32, sb - base));
+      }
+      // lane partials of the dense sums and of the rounds without ends are
+      // reduced together; run (warp-uniform) is added after the reduction
+#pragma unroll
+      for (int s = 0; s < NS; ++s) tot[C::smap(s)] = sacc[s];
+      warp_sum_some<M>(tot);
+#pragma unroll
+      for (int s = 0; s < NS; ++s) tot[C::smap(s)] = acc_add(run[s], tot[C::smap(s)]);
+      // the ends after the last nonzero of the range see the warp totals
+      for (; ec.kn < pf.k_hi; ++ec.kn)
         if (lane == 0)
 #pragma unroll
-          for (int s = 0; s < NS; ++s) rec[(size_t)ec.kn * M + C::smap(s)] = pref[s];
-        ++ec.kn;
-        next_end = ec.pos(P.gend);
+          for (int s = 0; s < NS; ++s) rec[(size_t)ec.kn * M + C::smap(s)] = tot[C::smap(s)];
+    } else {
+      const int sa = pf.sa, sb = pf.sb;
+      const int32_t* ri = pf.ri;
+      const T* vals = pf.vals;
+      A sacc[NS > 0 ? NS : 1];
+#pragma unroll
+      for (int s = 0; s < NS; ++s) acc_zero(sacc[s]);
+      EndCursor ec{pf.k_lo, pf.k_hi, pf.k_lo, pf.kreg};
+      int64_t next_end = ec.pos(P.gend);
+      auto round = [&](int row, T x, T ev, T wv, int nvalid) {
+        T sv[NS > 0 ? NS : 1];
+        sv[0] = ev * x;
+        if (NS > 1) sv[NS > 1 ? 1 : 0] = sv[0] * x;
+        if (NS > 2) {
+          sv[NS > 2 ? 2 : 0] = wv * sv[0];
+          sv[NS > 3 ? 3 : 0] = wv * sv[NS > 1 ? 1 : 0];
+        }
+        const int last_row = __shfl_sync(0xffffffffu, row, nvalid - 1);
+        // ends before the round's last nonzero see only part of the round
+        while (next_end < (int64_t)last_row) {
+          A pref[NS > 0 ? NS : 1];
+#pragma unroll
+          for (int s = 0; s < NS; ++s) pref[s] = acc_add_v(sacc[s], (int64_t)row <= next_end ? sv[s] : T(0));
+          warp_sum_some<(NS > 0 ? NS : 1)>(pref);
+          if (lane == 0)
+#pragma unroll
+            for (int s = 0; s < NS; ++s) rec[(size_t)ec.kn * M + C::smap(s)] = pref[s];
+          ++ec.kn;
+          next_end = ec.pos(P.gend);
+        }
+#pragma unroll
+        for (int s = 0; s < NS; ++s) sacc[s] = acc_add_v(sacc[s], sv[s]);
+      };
+      // e (and W) at the prefetched rows
+      T pe[SR], pw[SR];
+#pragma unroll
+      for (int r = 0; r < SR; ++r) {
+        const int row = pf.prow[r];
+        pe[r] = row == INT_MAX ? T(0) : ld_hint(e + row, keep);
+        pw[r] = (MODEL == 1 && row != INT_MAX) ? ld_hint(w2 + row, keep) : T(0);
       }
 #pragma unroll
-      for (int s = 0; s < NS; ++s) sacc[s] = acc_add_v(sacc[s], sv[s]);
-    };
-    // e (and W) at the prefetched rows
-    T pe[SR], pw[SR];
+      for (int r = 0; r < SR; ++r)
+        if (sa + 32 * r < sb) round(pf.prow[r], pf.pval[r], pe[r], pw[r], min(32, sb - sa - 32 * r));
+      for (int base = sa + 32 * SR; base < sb; base += 32) {
+        const int i = base + lane;
+        const bool valid = i < sb;
+        const int row = valid ? ld_hint(ri + i, strm) : INT_MAX;
+        const T x = valid ? (vals ? ld_stream(vals + i, strm) : T(1)) : T(0);
+        const T ev = valid ? ld_hint(e + row, keep) : T(0);
+        const T wv = (MODEL == 1 && valid) ? ld_hint(w2 + row, keep) : T(0);
+        round(row, x, ev, wv, min(32, sb - base));
+      }
 #pragma unroll
-    for (int r = 0; r < SR; ++r) {
-      const int row = pf.prow[r];
-      pe[r] = row == INT_MAX ? T(0) : ld_hint(e + row, keep);
-      pw[r] = (MODEL == 1 && row != INT_MAX) ? ld_hint(w2 + row, keep) : T(0);
+      for (int s = 0; s < NS; ++s) tot[C::smap(s)] = sacc[s];  // lane partials, reduced below
+      // warp totals, then the ends after the last nonzero of the range see them
+      warp_sum_some<M>(tot);
+      for (; ec.kn < pf.k_hi; ++ec.kn)
+        if (lane == 0)
+#pragma unroll
+          for (int s = 0; s < NS; ++s) rec[(size_t)ec.kn * M + C::smap(s)] = tot[C::smap(s)];
     }
-#pragma unroll
-    for (int r = 0; r < SR; ++r)
-      if (sa + 32 * r < sb) round(pf.prow[r], pf.pval[r], pe[r], pw[r], min(32, sb - sa - 32 * r));
-    for (int base = sa + 32 * SR; base < sb; base += 32) {
-      const int i = base + lane;
-      const bool valid = i < sb;
-      const int row = valid ? ld_hint(ri + i, strm) : INT_MAX;
-      const T x = valid ? (vals ? ld_stream(vals + i, strm) : T(1)) : T(0);
-      const T ev = valid ? ld_hint(e + row, keep) : T(0);
-      const T wv = (MODEL == 1 && valid) ? ld_hint(w2 + row, keep) : T(0);
-      round(row, x, ev, wv, min(32, sb - base));
-    }
-#pragma unroll
-    for (int s = 0; s < NS; ++s) tot[C::smap(s)] = sacc[s];  // lane partials, reduced below
-    // warp totals, then the ends after the last nonzero of the range see them
-    warp_sum_some<M>(tot);
-    for (; ec.kn < pf.k_hi; ++ec.kn)
-      if (lane == 0)
-#pragma unroll
-        for (int s = 0; s < NS; ++s) rec[(size_t)ec.kn * M + C::smap(s)] = tot[C::smap(s)];
   } else {
     warp_sum_some<M>(tot);
   }

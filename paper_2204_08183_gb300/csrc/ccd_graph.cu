@@ -117,7 +117,9 @@ __global__ void k_graph_init(const __grid_constant__ CcdParams P0) {
   L->eta_updates = 0;
 }
 
-template <int MODEL, int LAYOUT, typename T, bool BATCH>
+// MULTI selects the group-end handling for warps that hold many ends (see
+// warp_pass); the host picks it when the tie groups outnumber the warps.
+template <int MODEL, int LAYOUT, typename T, bool BATCH, bool MULTI>
 __global__ void __launch_bounds__(GCfg<MODEL, LAYOUT>::NT, GCfg<MODEL, LAYOUT>::MINB)
     k_pass(const __grid_constant__ CcdParams P0, int j) {
   using A = typename AccOf<T>::type;
@@ -169,7 +171,7 @@ __global__ void __launch_bounds__(GCfg<MODEL, LAYOUT>::NT, GCfg<MODEL, LAYOUT>::
   // ------------------------------------------- step 2 for coordinate j
   A* rec = reinterpret_cast<A*>(P.rec);
   A tot[M];
-  warp_pass<MODEL, LAYOUT, T, GC::U, GC::SR>(P, j, row_lo, row_hi, rec, tot, pf);
+  warp_pass<MODEL, LAYOUT, T, GC::U, GC::SR, MULTI>(P, j, row_lo, row_hi, rec, tot, pf);
   pdl_launch_dependents();
   if (lane == 0)
 #pragma unroll
@@ -516,7 +518,7 @@ cudaError_t grid_graph(int* G, int* wpc) {
   cudaError_t st = cudaGetDevice(&dev);
   if (st != cudaSuccess) return st;
   if ((st = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return st;
-  if ((st = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pass<MODEL, LAYOUT, T, false>, GC::NT, 0)) !=
+  if ((st = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pass<MODEL, LAYOUT, T, false, false>, GC::NT, 0)) !=
       cudaSuccess)
     return st;
   if (occ < 1) return cudaErrorLaunchOutOfResources;
@@ -543,12 +545,17 @@ cudaError_t capture_sweep(const CcdParams& P, bool pdl, cudaStream_t cs, cudaGra
   ct.blockDim = dim3(kTransThreads);
   // batched fits: Cox only (the censoring weights of Fine-Gray would have
   // to be re-estimated on each training set)
-  auto kp = k_pass<MODEL, LAYOUT, T, false>;
+  // Cox passes whose warps hold two group ends or more on average take the
+  // many-ends form of the row pass
+  auto kp = k_pass<MODEL, LAYOUT, T, false, false>;
   auto kt = k_trans<MODEL, LAYOUT, T, false>;
   if constexpr (MODEL == 0) {
+    const bool multi = (int64_t)P.K >= 2 * (int64_t)P.nwarps;
     if (P.nfit > 0) {
-      kp = k_pass<MODEL, LAYOUT, T, true>;
+      kp = multi ? k_pass<MODEL, LAYOUT, T, true, true> : k_pass<MODEL, LAYOUT, T, true, false>;
       kt = k_trans<MODEL, LAYOUT, T, true>;
+    } else if (multi) {
+      kp = k_pass<MODEL, LAYOUT, T, false, true>;
     }
   } else {
     if (P.nfit > 0) {
@@ -606,6 +613,35 @@ void graph_cache_free(GraphCache* gc) {
   if (gc->flag) cudaFreeHost(gc->flag);
   if (gc->cs) cudaStreamDestroy(gc->cs);
   *gc = GraphCache();
+}
+
+cudaError_t time_one_sweep(int model, int layout, int prec, const CcdParams& P, cudaStream_t s, float* ms) {
+  *ms = 0.f;
+  GraphCache gc;
+  struct Guard {
+    GraphCache* g;
+    cudaGraph_t graph = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~Guard() {
+      if (graph) cudaGraphDestroy(graph);
+      if (a) cudaEventDestroy(a);
+      if (b) cudaEventDestroy(b);
+      graph_cache_free(g);
+    }
+  } guard{&gc};
+  cudaError_t st;
+  if ((st = cudaStreamCreateWithFlags(&gc.cs, cudaStreamNonBlocking)) != cudaSuccess) return st;
+  const char* env = std::getenv("SURVGPU_GRAPH_PDL");
+  const bool pdl = !(env && env[0] == '0');
+  if ((st = capture_any(model, layout, prec, P, pdl, gc.cs, &guard.graph)) != cudaSuccess) return st;
+  if ((st = cudaGraphInstantiate(&gc.exec, guard.graph, 0)) != cudaSuccess) return st;
+  if ((st = cudaEventCreate(&guard.a)) != cudaSuccess) return st;
+  if ((st = cudaEventCreate(&guard.b)) != cudaSuccess) return st;
+  if ((st = cudaEventRecord(guard.a, s)) != cudaSuccess) return st;
+  if ((st = cudaGraphLaunch(gc.exec, s)) != cudaSuccess) return st;
+  if ((st = cudaEventRecord(guard.b, s)) != cudaSuccess) return st;
+  if ((st = cudaEventSynchronize(guard.b)) != cudaSuccess) return st;
+  return cudaEventElapsedTime(ms, guard.a, guard.b);
 }
 
 cudaError_t run_ccd_graph(int model, int layout, int prec, const CcdParams& P, cudaStream_t s, GraphCache* gc,

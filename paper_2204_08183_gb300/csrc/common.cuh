@@ -138,6 +138,17 @@ static __device__ __noinline__ double warp_sum_dd(double v) {
   for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
   return __shfl_sync(0xffffffffu, v, 0);
 }
+// Plain FP32 / FP64 sum over the lanes, same tree shape (result in every lane).
+__device__ __forceinline__ float warp_sum_t(float v) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
+  return __shfl_sync(0xffffffffu, v, 0);
+}
+__device__ __forceinline__ double warp_sum_t(double v) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
+  return __shfl_sync(0xffffffffu, v, 0);
+}
 __device__ __forceinline__ ff warp_sum(ff v) { return warp_sum_ff(v); }
 __device__ __forceinline__ double warp_sum(double v) { return warp_sum_dd(v); }
 

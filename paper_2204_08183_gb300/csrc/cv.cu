@@ -108,11 +108,11 @@ __global__ void k_cv_dtx_dense(const T* X, int64_t ld, int64_t n, const int8_t* 
 
 // eta = 0 and e = 1 (0 for the subjects of the fit's fold), fit = blockIdx.y
 template <typename T, typename E>
-__global__ void k_cv_init(int64_t n, const int8_t* fold_id, int nfolds, T* e, E* eta) {
+__global__ void k_cv_init(int64_t n, int64_t fit_n, const int8_t* fold_id, int nfolds, T* e, E* eta) {
   const int f = blockIdx.y;
   const int fold = f % nfolds;
-  T* ef = e + (size_t)f * n;
-  E* etaf = eta + (size_t)f * n;
+  T* ef = e + (size_t)f * fit_n;
+  E* etaf = eta + (size_t)f * fit_n;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     ef[i] = fold_id[i] == fold ? T(0) : T(1);
     etaf[i] = E{};
@@ -139,7 +139,8 @@ __device__ __forceinline__ double eta_d(double q) { return q; }
 // den_g at each group end (stored to den[f][g]); a second loop takes the
 // FP64 logs.
 template <typename T, typename E>
-__global__ void __launch_bounds__(kScanThreads) k_cv_heldout(int64_t n, const int32_t* time, const int8_t* status,
+__global__ void __launch_bounds__(kScanThreads) k_cv_heldout(int64_t n, int64_t fit_n, const int32_t* time,
+                                                              const int8_t* status,
                                                               const int8_t* fold_id, int nfolds, const E* eta_all,
                                                               const int32_t* dk_all, const int32_t* dk_fold,
                                                               int32_t K, double* den_all, double* heldout) {
@@ -149,7 +150,7 @@ __global__ void __launch_bounds__(kScanThreads) k_cv_heldout(int64_t n, const in
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int f = blockIdx.x;
   const int fold = f % nfolds;
-  const E* eta = eta_all + (size_t)f * n;
+  const E* eta = eta_all + (size_t)f * fit_n;
   double* den = den_all + (size_t)f * K;
   A carry;
   acc_zero(carry);
@@ -368,23 +369,25 @@ cudaError_t cv_dtx(int layout, int prec, const int64_t* col_ptr, const int32_t* 
   return cudaGetLastError();
 }
 
-cudaError_t cv_init(int prec, int64_t n, const int8_t* fold_id, int nfolds, int nfit, void* e, void* eta,
-                    cudaStream_t s) {
+cudaError_t cv_init(int prec, int64_t n, int64_t fit_n, const int8_t* fold_id, int nfolds, int nfit, void* e,
+                    void* eta, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const dim3 g(grid_for(n, kCvThreads, std::max<int64_t>(1, 8192 / nfit)), nfit);
-  if (prec == 0) k_cv_init<float, float2><<<g, kCvThreads, 0, s>>>(n, fold_id, nfolds, (float*)e, (float2*)eta);
-  else k_cv_init<double, double><<<g, kCvThreads, 0, s>>>(n, fold_id, nfolds, (double*)e, (double*)eta);
+  if (prec == 0)
+    k_cv_init<float, float2><<<g, kCvThreads, 0, s>>>(n, fit_n, fold_id, nfolds, (float*)e, (float2*)eta);
+  else
+    k_cv_init<double, double><<<g, kCvThreads, 0, s>>>(n, fit_n, fold_id, nfolds, (double*)e, (double*)eta);
   return cudaGetLastError();
 }
 
-cudaError_t cv_heldout(int prec, int64_t n, const int32_t* time, const int8_t* status, const int8_t* fold_id,
+cudaError_t cv_heldout(int prec, int64_t n, int64_t fit_n, const int32_t* time, const int8_t* status, const int8_t* fold_id,
                        int nfolds, int nfit, const void* eta, const int32_t* dk_all, const int32_t* dk_fold,
                        int32_t K, double* den, double* heldout, cudaStream_t s) {
   if (prec == 0)
-    k_cv_heldout<float, float2><<<nfit, kScanThreads, 0, s>>>(n, time, status, fold_id, nfolds, (const float2*)eta,
+    k_cv_heldout<float, float2><<<nfit, kScanThreads, 0, s>>>(n, fit_n, time, status, fold_id, nfolds, (const float2*)eta,
                                                               dk_all, dk_fold, K, den, heldout);
   else
-    k_cv_heldout<double, double><<<nfit, kScanThreads, 0, s>>>(n, time, status, fold_id, nfolds, (const double*)eta,
+    k_cv_heldout<double, double><<<nfit, kScanThreads, 0, s>>>(n, fit_n, time, status, fold_id, nfolds, (const double*)eta,
                                                                dk_all, dk_fold, K, den, heldout);
   return cudaGetLastError();
 }

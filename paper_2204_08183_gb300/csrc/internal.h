@@ -177,6 +177,9 @@ cudaError_t graph_init(const CcdParams& P, cudaStream_t s);
 cudaError_t run_ccd_graph(int model, int layout, int prec, const CcdParams& P, cudaStream_t s, GraphCache* gc,
                           cudaEvent_t t0, int* replays, int* launches);
 void graph_cache_free(GraphCache* gc);
+// One replay of the sweep graph of P (captured and destroyed here), timed
+// with events on s: *ms.  P's state must be initialised (graph_init).
+cudaError_t time_one_sweep(int model, int layout, int prec, const CcdParams& P, cudaStream_t s, float* ms);
 
 // ---- prep kernels (prep.cu) --------------------------------------------
 cudaError_t prep_check_times(const int32_t* time, const int8_t* status, int64_t n, int model,
@@ -226,12 +229,13 @@ cudaError_t cv_fold_stats(const int32_t* gend, int32_t K, const int8_t* status, 
 cudaError_t cv_dtx(int layout, int prec, const int64_t* col_ptr, const int32_t* row_idx, const void* values,
                    int64_t ld, int64_t n, int64_t p, const int8_t* status, const int8_t* fold_id, int nfolds,
                    double* dTx, cudaStream_t s);
-// e [nfit][n] = 1 outside the fit's fold (f % nfolds), 0 inside; eta [nfit][n] = 0
-cudaError_t cv_init(int prec, int64_t n, const int8_t* fold_id, int nfolds, int nfit, void* e, void* eta,
-                    cudaStream_t s);
+// e [nfit][fit_n] = 1 outside the fit's fold (f % nfolds), 0 inside; eta = 0
+// (rows 0..n-1 of each fit; fit_n >= n is the per-fit stride)
+cudaError_t cv_init(int prec, int64_t n, int64_t fit_n, const int8_t* fold_id, int nfolds, int nfit, void* e,
+                    void* eta, cudaStream_t s);
 // heldout [nfit]: log partial likelihood of each fit's fold on its own risk
-// sets at eta [nfit][n]; den [nfit][K] scratch
-cudaError_t cv_heldout(int prec, int64_t n, const int32_t* time, const int8_t* status, const int8_t* fold_id,
+// sets at eta [nfit][fit_n]; den [nfit][K] scratch
+cudaError_t cv_heldout(int prec, int64_t n, int64_t fit_n, const int32_t* time, const int8_t* status, const int8_t* fold_id,
                        int nfolds, int nfit, const void* eta, const int32_t* dk_all, const int32_t* dk_fold,
                        int32_t K, double* den, double* heldout, cudaStream_t s);
 // cv_mean [nlambda] and *best (device)

@@ -33,6 +33,10 @@ struct surv_workspace {
   int64_t nll_n = -1;
   int32_t nll_p = 0, nll_c = 0, nll_K = 0, nll_G = 0, nll_wpc = 0, nll_wpw = 0;
   const void* nll_x = nullptr;
+  // CTAs per fit chosen by the cross-validation tuner, and the shape it was
+  // tuned for (n, p, fits, layout * 2 + precision, dtype, layout tag)
+  int32_t cv_tuned_ctas = 0;
+  int64_t cv_tune_key[6] = {0, 0, 0, 0, 0, 0};
 };
 
 namespace survgpu {

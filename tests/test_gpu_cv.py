@@ -73,6 +73,22 @@ def test_cv_fold_fit_equals_plain_fit_of_subset(lib):
         np.testing.assert_allclose(r["beta"][0, k], b, rtol=0, atol=2e-6)
 
 
+def test_cv_tuner_picks_a_candidate_and_is_reused(lib):
+    d = small_csc(20000, 6, seed=33, density=0.2, n_times=500)
+    fold = synth.cv_folds(20000, 5, seed=34)
+    sd = survdata(d)
+    ws = binding.Workspace()
+    lam = [50.0, 5.0, 0.5]
+    r = binding.cox_cv_path(sd, fold, 5, lam, penalty="l1", tol=1e-9, workspace=ws, flags=binding.SURV_FLAG_CV_TUNE)
+    g = r["info"]["ctas_per_fit"]
+    assert g >= 1
+    r2 = binding.cox_cv_path(sd, fold, 5, lam, penalty="l1", tol=1e-9, workspace=ws)
+    assert r2["info"]["ctas_per_fit"] == g
+    np.testing.assert_array_equal(r["beta"], r2["beta"])
+    ref = oracle.cv_path(d["time"], d["status"], oracle_X(d), fold, 5, lam, "l1", sweeps=r["sweeps"])
+    np.testing.assert_allclose(r["beta"], ref["beta"], rtol=0, atol=TOL_B["f32c"])
+
+
 def test_cv_path_all_fits_stop_at_lambda_max(lib):
     d = small_csc(2000, 6, seed=27, density=0.3, n_times=100)
     fold = synth.cv_folds(2000, 5, seed=28)
