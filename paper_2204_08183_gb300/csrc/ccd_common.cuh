@@ -268,49 +268,54 @@ __device__ __forceinline__ void warp_pass(const CcdParams& P, int j, int64_t row
     auto tile = [&](int64_t t0, const T (&ev)[U][VEC], const T (&xv)[U][VEC], const T (&wv)[U][VEC]) {
       const int64_t t_end = min(t0 + (int64_t)TILE, row_hi);
       if constexpr (ND == 1 && MULTI) {
-        T su[U];
+        // acc[0] is the warp-uniform sum of the rows before the tile.  One
+        // FP32 lane scan per chunk row u gives every chunk's tile-relative
+        // exclusive prefix; the lane that owns an end's chunk adds the rows
+        // of the chunk up to the end and writes the record.
+        T su[U], ex[U], tu[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) su[u] = chunk_sum(0, ev, xv, wv, u);
-        auto share = [&](int64_t end) {
-          const int off = (int)(end - t0);
-          const int cstar = off / VEC, qstar = off - cstar * VEC;
-          T part = T(0);
+#pragma unroll
+        for (int u = 0; u < U; ++u) ex[u] = su[u];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1)
 #pragma unroll
           for (int u = 0; u < U; ++u) {
-            const int c = 32 * u + lane;
-            if (c < cstar) {
-              part += su[u];
-            } else if (c == cstar) {
+            const T t = __shfl_up_sync(0xffffffffu, ex[u], d);
+            if (lane >= d) ex[u] += t;
+          }
 #pragma unroll
-              for (int q = 0; q < VEC; ++q)
-                if (q <= qstar) part += dense_comp<MODEL, LAYOUT, T>(0, ev[u][q], xv[u][q], wv[u][q]);
-            }
-          }
-          return part;
-        };
-        if (next_end < t_end) {
-          if (!ec.second_before(t_end)) {
-            A pref[1] = {acc_add_v(acc[0], share(next_end))};
-            warp_sum_some<1>(pref);
-            if (lane == 0) rec[(size_t)ec.kn * M + C::dmap(0)] = pref[0];
-            ++ec.kn;
-            next_end = ec.pos(P.gend);
-          } else {
-            A base[1] = {acc[0]};
-            warp_sum_some<1>(base);
-            do {
-              const A pref = acc_add_v(base[0], warp_sum_t(share(next_end)));
-              if (lane == 0) rec[(size_t)ec.kn * M + C::dmap(0)] = pref;
-              ++ec.kn;
-              next_end = ec.pos(P.gend);
-            } while (next_end < t_end);
-          }
+        for (int u = 0; u < U; ++u) {
+          tu[u] = __shfl_sync(0xffffffffu, ex[u], 31);  // chunk row total
+          const T t = __shfl_up_sync(0xffffffffu, ex[u], 1);
+          ex[u] = lane == 0 ? T(0) : t;                  // lanes before, same u
         }
+        while (next_end < t_end) {
+          const int off = (int)(next_end - t0);
+          const int cstar = off / VEC, qstar = off - cstar * VEC;
+          if ((cstar & 31) == lane) {
+            const int ustar = cstar >> 5;
+            T pre = T(0);
 #pragma unroll
-        for (int s = 1; s < U; s <<= 1)
+            for (int u = 0; u < U; ++u) {
+              if (u < ustar) pre += tu[u];
+              if (u == ustar) {
+                T in = ex[u];
 #pragma unroll
-          for (int u = 0; u + s < U; u += 2 * s) su[u] += su[u + s];
-        acc[0] = acc_add_v(acc[0], su[0]);
+                for (int q = 0; q < VEC; ++q)
+                  if (q <= qstar) in += dense_comp<MODEL, LAYOUT, T>(0, ev[u][q], xv[u][q], wv[u][q]);
+                pre += in;
+              }
+            }
+            rec[(size_t)ec.kn * M + C::dmap(0)] = acc_add_v(acc[0], pre);
+          }
+          ++ec.kn;
+          next_end = ec.pos(P.gend);
+        }
+        T tt = tu[0];
+#pragma unroll
+        for (int u = 1; u < U; ++u) tt += tu[u];
+        acc[0] = acc_add_v(acc[0], tt);
       } else {
         while (next_end < t_end) {
           A pref[ND];
@@ -353,7 +358,7 @@ __device__ __forceinline__ void warp_pass(const CcdParams& P, int j, int64_t row
       tile(t0, ev, xv, wv);
     }
 #pragma unroll
-    for (int d = 0; d < ND; ++d) tot[C::dmap(d)] = acc[d];  // lane partials, reduced below
+    for (int d = 0; d < ND; ++d) tot[C::dmap(d)] = acc[d];  // lane partials (MULTI, ND = 1: the warp sum)
   }
   if (LAYOUT == 0 && NS > 0) {
     // sparse part: the nonzeros of column j inside the warp's rows
@@ -478,11 +483,14 @@ __device__ __forceinline__ void warp_pass(const CcdParams& P, int j, int64_t row
         }
         round(row, x, ev, wv, min(32, sb - base));
       }
-      // lane partials of the dense sums and of the rounds without ends are
-      // reduced together; run (warp-uniform) is added after the reduction
+      // lane partials of the rounds without ends are reduced; run and the
+      // dense sum (both warp-uniform) are added after the reduction
 #pragma unroll
       for (int s = 0; s < NS; ++s) tot[C::smap(s)] = sacc[s];
+      const A dense_run = tot[C::dmap(0)];
+      acc_zero(tot[C::dmap(0)]);
       warp_sum_some<M>(tot);
+      tot[C::dmap(0)] = dense_run;
 #pragma unroll
       for (int s = 0; s < NS; ++s) tot[C::smap(s)] = acc_add(run[s], tot[C::smap(s)]);
       // the ends after the last nonzero of the range see the warp totals
