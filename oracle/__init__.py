@@ -14,3 +14,4 @@ Parity status of each function is listed in ``oracle/survival.py``'s header.
 from .survival import *  # noqa: F401,F403
 from .nll import *  # noqa: F401,F403
 from .cv import *  # noqa: F401,F403
+from .sparse_numerator import *  # noqa: F401,F403
