@@ -37,6 +37,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "CCD sweeps/s, Cox N=1e7 p=100 5% binary CSC, L1 lambda=1e-4*N"
+SN_METRIC = METRIC + ", sparse-numerator form (not the paper's method)"
 UNIT = "sweeps/s"
 SEED = 2
 
@@ -51,11 +52,15 @@ def parse():
     ap.add_argument("--p", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["ccd", "autograd", "cv"], default="ccd",
+    ap.add_argument("--workload", choices=["ccd", "autograd", "cv", "sn"], default="ccd",
                     help="ccd: the headline penalised Cox fit; autograd: forward + backward of the "
                          "differentiable Cox NLL at N=2^22, p=256, 64 columns (bf16 X); cv: 10-fold "
-                         "cross-validation x 20 L1 strengths (200 Cox fits) at N=1e6, p=500, 1%% binary")
+                         "cross-validation x 20 L1 strengths (200 Cox fits) at N=1e6, p=500, 1%% binary; "
+                         "sn: the headline fit in the sparse-numerator form (not the paper's method, "
+                         "reported separately)")
     ap.add_argument("--ctas", type=int, default=0, help="cv: CTAs per fit (0 = the library's choice)")
+    ap.add_argument("--cv-p", type=int, default=500, help="cv: covariates (500 = the benchmarked size; smaller "
+                                                           "values give small cases for profiling)")
     ap.add_argument("--no-sequential", action="store_true", help="cv: skip the 200 sequential plain fits")
     ap.add_argument("--schedule", choices=["graph", "persistent"], default="graph",
                     help="graph: two kernels per coordinate replayed as a CUDA graph (default); "
@@ -161,8 +166,11 @@ def run_gpu(args, rank, world):
                           values=dev(d["values"]), n=n, p=p)
     ws = binding.Workspace()
     stream = torch.cuda.current_stream()
-    kw = dict(penalty="l1", lam=lam, tol=1e-8, max_sweeps=1000, workspace=ws,
-              flags=binding.SURV_FLAG_PERSISTENT if args.schedule == "persistent" else 0)
+    sn = args.workload == "sn"
+    flags = binding.SURV_FLAG_PERSISTENT if args.schedule == "persistent" else 0
+    if sn:
+        flags = binding.SURV_FLAG_SPARSE_NUMERATOR
+    kw = dict(penalty="l1", lam=lam, tol=1e-8, max_sweeps=1000, workspace=ws, flags=flags)
     beta_dev = torch.zeros(p, dtype=torch.float64, device="cuda")
     # the sampler starts before the warm-up so that its start-up cannot fall
     # inside the timed region; its samples cover warm-up and timed fits
@@ -215,6 +223,13 @@ def run_gpu(args, rank, world):
     per_pass = 4 * n + 8 * nnz / p + 8 * K          # e stream + column j (row, value) + group table
     per_update = 28 * nnz / p                         # row, value, eta r/w (8+8), e write
     alg_bytes = passes * per_pass + upd * per_update
+    if sn:
+        # per coordinate: column j (row, value) and, per nonzero, e, its
+        # group, Lambda and W (4 + 4 + 8 + 8); per rebuild of the risk sets
+        # (one per nonzero step, plus the first): e over all rows and the
+        # group table (Den, v1, v2, Lambda, W, d)
+        per_pass = 32 * nnz / p
+        alg_bytes = passes * per_pass + upd * per_update + (upd + len(infos)) * (4 * n + 44 * K)
     kern_ms = sum(i["ccd_kernel_ms"] for i in infos)
     peaks = {}
     try:
@@ -231,7 +246,7 @@ def run_gpu(args, rank, world):
                 "algorithmic_bytes_per_coordinate": round(alg_bytes / passes),
                 "us_per_coordinate": round(us_per_coord, 3),
                 "passes_per_fit": passes / len(infos), "eta_updates_per_fit": upd / len(infos)}
-    if args.schedule == "graph" and n == 10_000_000 and p == 100:
+    if args.schedule == "graph" and n == 10_000_000 and p == 100 and not sn:
         # dram__bytes_read.sum + dram__bytes_write.sum of k_pass + k_trans per
         # coordinate, steady state (ncu --cache-control none, one pass); see
         # profiles/k_pass_k_trans_cox_csc_n1e7.md.  e stays in L2 across
@@ -242,6 +257,10 @@ def run_gpu(args, rank, world):
         roofline["traffic"] = None
     roofline["kernel"] = ("ccd_kernel<cox,csc,f32> (persistent, one launch per fit)" if args.schedule == "persistent"
                           else "k_pass + k_trans <cox,csc,f32>, one pair per coordinate, one graph replay per sweep")
+    if sn:
+        roofline["kernel"] = ("k_sn_den_a/den_b/lam (after nonzero steps only) + k_sn_col_a/col_b per coordinate, "
+                              "one graph replay per sweep")
+        roofline["unit_of_work"] = "one coordinate (column pass; risk-set rebuild after nonzero steps)"
     if args.schedule == "persistent":
         roofline["phase_ms_per_launch"] = {k: round(sum(i["phase_ms"][q] for i in infos) / len(infos), 4)
                                            for q, k in enumerate(["pass_cta0", "ex1_arrive", "ex1_wait",
@@ -251,7 +270,8 @@ def run_gpu(args, rank, world):
                                                                   "pass_mean_cta", "dense_max_cta",
                                                                   "sparse_max_cta", "ex1_sums", "ex1_stores"])}
 
-    out = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+    out = {"metric": SN_METRIC if sn else METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+           "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 3), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": config_dict(n, p, lam), "roofline": roofline, "clocks": clk, "gpu_launches": launches,
@@ -259,6 +279,8 @@ def run_gpu(args, rank, world):
                    "nnz_beta": infos[-1]["nnz_beta"], "loglik": infos[-1]["loglik"], "n_groups": K,
                    "ms_per_fit": round(t_max / args.steps, 3)}}
 
+    if sn:
+        out["config"]["workload"] += "_sparse_numerator"
     # end to end: host (pinned) buffers through the same C ABI call
     if not args.no_e2e:
         host = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
@@ -286,7 +308,7 @@ def run_gpu(args, rank, world):
                       "note": "cox_fit with pinned host arrays: the library copies them to the device, fits, "
                               "and copies beta back inside the call"}
 
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not sn:
         sps, dt, npass = oracle_sample(d, lam, 6)
         out["cpu_baseline"] = {"value": round(sps, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
                                "sample": "oracle.ccd_fit, one sweep over the first 6 of 100 columns at "
@@ -415,9 +437,9 @@ def run_autograd(args, rank, world):
 CV_METRIC = "CV fits/s, Cox 10-fold x 20 L1 lambdas (200 fits), N=1e6 p=500 1% binary CSC"
 
 
-def cv_workload():
+def cv_workload(p=500):
     from paper_2204_08183_gb300 import synth
-    d = synth.cohort_cox_sparse(1_000_000, 500, seed=41, density=0.01, n_true=10, laplace_scale=0.2,
+    d = synth.cohort_cox_sparse(1_000_000, p, seed=41, density=0.01, n_true=10, laplace_scale=0.2,
                                 censor_frac=0.4, grid=3650)
     fold = synth.cv_folds(1_000_000, 10, seed=42)
     return d, fold
@@ -435,7 +457,7 @@ def run_cv(args, rank, world):
     import __graft_entry__
     __graft_entry__.build()
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
-    d, fold = cv_workload()
+    d, fold = cv_workload(args.cv_p)
     n, p = d["n"], d["p"]
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
     sd = binding.SurvData(dev(d["time"]), dev(d["status"]), col_ptr=dev(d["col_ptr"]), row_idx=dev(d["row_idx"]),
@@ -498,7 +520,7 @@ def run_cv(args, rank, world):
     out = {"metric": CV_METRIC, "value": round(value, 2), "unit": "fits/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 3), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": "cox_cv10x20_l1_csc_n1000000_p500", "n": n, "p": p, "density": 0.01,
+           "config": {"workload": "cox_cv10x20_l1_csc_n1000000_p%d" % p, "n": n, "p": p, "density": 0.01,
                       "folds": 10, "fold_sizes": [int(x) for x in np.bincount(fold, minlength=10)],
                       "lambdas": 20, "lambda_max": lmax, "lambda_ratio": 1e-3, "tol": 1e-8, "censoring": 0.4,
                       "time_grid": 3650, "start": "cold (beta = 0) for every fit",
@@ -644,6 +666,8 @@ def main():
         out = run_autograd(args, rank, world)
     elif args.workload == "cv":
         out = run_cv(args, rank, world)
+    elif args.workload == "sn":
+        out = run_gpu(args, rank, world)
     else:
         out = run_gpu(args, rank, world)
     if rank == 0 and out is not None:

@@ -129,6 +129,19 @@ typedef struct surv_opts {
  * keep that count in the workspace for later calls with the same shape
  * (n, p, number of fits, layout, precision). */
 #define SURV_FLAG_CV_TUNE 4
+/* cox_fit only (CSC data, SURV_PREC_F32C): the sparse-numerator form, not
+ * in the paper.  The same CCD with the same l'_j and l''_j, computed from
+ * the nonzeros of column j alone:
+ *   sum_k d_k N1_k/Den_k = sum_t x_t e_t Lambda(g_t),
+ *   sum_k d_k N2_k/Den_k = sum_t x_t^2 e_t Lambda(g_t),
+ *   sum_k d_k (N1_k/Den_k)^2 = sum_t C_t^2 [W(g_{t+1}) - W(g_t)],
+ * with Lambda(g) = sum_{k >= g} d_k/Den_k, W(g) = sum_{k < g} d_k/Den_k^2,
+ * C_t the running sum of x e over the column's nonzeros (rows increasing)
+ * and g_t the tie group of row t.  The risk-set sums Den_k, Lambda and W
+ * are rebuilt with a pass over all subjects only after a nonzero step, so a
+ * coordinate whose step is zero costs O(nnz_j).  Its speed is reported
+ * separately from the paper's method. */
+#define SURV_FLAG_SPARSE_NUMERATOR 8
 
 /* Fill *opts with defaults: no penalty, FP32-compensated precision,
  * tol 1e-8, max_sweeps 1000, default stream, no workspace. */

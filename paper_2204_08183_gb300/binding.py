@@ -39,6 +39,7 @@ SURV_PREC = {"f32c": 0, "f64": 1}
 SURV_FLAG_TEST_STALL = 1
 SURV_FLAG_PERSISTENT = 2
 SURV_FLAG_CV_TUNE = 4
+SURV_FLAG_SPARSE_NUMERATOR = 8
 
 # exported symbols, in the order the header declares them
 EXPORTS = ["surv_opts_default", "surv_workspace_create", "surv_workspace_destroy", "surv_sort_desc",

@@ -266,7 +266,14 @@ int fit_common(int model, const surv_data* d, const surv_opts* o_in, double* bet
   if (d->dtype != SURV_F32 && d->dtype != SURV_F64) { set_error("bad dtype"); return SURV_E_INVALID; }
   if (o.penalty < 0 || o.penalty > 2 || o.precision < 0 || o.precision > 1) { set_error("bad penalty/precision"); return SURV_E_INVALID; }
   if (!(o.lambda >= 0.0) || !std::isfinite(o.lambda) || !(o.tol >= 0.0) || o.max_sweeps < 0) { set_error("bad lambda/tol/max_sweeps"); return SURV_E_INVALID; }
-  if ((o.flags & ~(SURV_FLAG_TEST_STALL | SURV_FLAG_PERSISTENT)) != 0) { set_error("unknown flags"); return SURV_E_INVALID; }
+  if ((o.flags & ~(SURV_FLAG_TEST_STALL | SURV_FLAG_PERSISTENT | SURV_FLAG_SPARSE_NUMERATOR)) != 0) { set_error("unknown flags"); return SURV_E_INVALID; }
+  // the sparse-numerator form: Cox, CSC, FP32 mode, a full fit on the default schedule
+  const bool sn = (o.flags & SURV_FLAG_SPARSE_NUMERATOR) != 0;
+  if (sn && (model != SURV_COX || d->layout != SURV_CSC || o.precision != SURV_PREC_F32C || single_j >= 0 ||
+             (o.flags & (SURV_FLAG_TEST_STALL | SURV_FLAG_PERSISTENT)) != 0)) {
+    set_error("SURV_FLAG_SPARSE_NUMERATOR needs a Cox fit of CSC data in the FP32 mode on the default schedule");
+    return SURV_E_INVALID;
+  }
   if (single_j >= 0 && single_j >= p) { set_error("coordinate j=%d out of range", single_j); return SURV_E_INVALID; }
   if (n == 0) { set_error("no subjects"); return SURV_E_NO_EVENTS; }
   if (!d->time || !d->status) { set_error("null time/status"); return SURV_E_INVALID; }
@@ -358,6 +365,35 @@ int fit_common(int model, const surv_data* d, const surv_opts* o_in, double* bet
   void* aggr = nullptr;
   if (graph && (rc = ensure(ws, W::WT, 8 * (size_t)M * nwarps, &wt))) return rc;
   if (graph && (rc = ensure(ws, W::AGG, 8 * (size_t)survgpu::kRep * M * G, &aggr))) return rc;
+  survgpu::SnParams S;
+  std::memset(&S, 0, sizeof(S));
+  if (sn) {
+    void *grp, *den, *v1, *v2, *lamv, *Wv, *pden, *ll, *pcol;
+    if ((rc = ensure(ws, W::SN_GRP, 4 * (size_t)n, &grp))) return rc;
+    if ((rc = ensure(ws, W::SN_DEN, 8 * (size_t)K, &den))) return rc;
+    if ((rc = ensure(ws, W::SN_V1, 8 * (size_t)K, &v1))) return rc;
+    if ((rc = ensure(ws, W::SN_V2, 8 * (size_t)K, &v2))) return rc;
+    if ((rc = ensure(ws, W::SN_LAM, 8 * (size_t)K, &lamv))) return rc;
+    if ((rc = ensure(ws, W::SN_W, 8 * (size_t)(K + 1), &Wv))) return rc;
+    if ((rc = ensure(ws, W::SN_PDEN, 8 * 3 * (size_t)G, &pden))) return rc;
+    if ((rc = ensure(ws, W::SN_LL, 8, &ll))) return rc;
+    // column kernels: at most 8 entries per thread of 256 (the longest column)
+    int64_t maxnnz = 0;
+    for (int64_t j = 0; j < p; ++j) maxnnz = std::max(maxnnz, colptr_h[j + 1] - colptr_h[j]);
+    const int G2 = (int)std::max<int64_t>(G, (maxnnz + 2047) / 2048);
+    if ((rc = ensure(ws, W::SN_PCOL, 8 * 4 * (size_t)G2, &pcol))) return rc;
+    S.grp = static_cast<const int32_t*>(grp);
+    S.den = static_cast<double*>(den);
+    S.v1 = static_cast<double*>(v1);
+    S.v2 = static_cast<double*>(v2);
+    S.lam = static_cast<float2*>(lamv);
+    S.W = static_cast<float2*>(Wv);
+    S.part_den = static_cast<double*>(pden);
+    S.ll_den = static_cast<double*>(ll);
+    S.part_col = static_cast<uint64_t*>(pcol);
+    S.G2 = G2;
+    S.multi = (int64_t)K >= 2 * (int64_t)nwarps ? 1 : 0;
+  }
 
   CUDA_TRY(survgpu::prep_write_ends(time_p, n, static_cast<const int32_t*>(blockcnt), static_cast<int32_t*>(gend), s));
   CUDA_TRY(survgpu::prep_group_stats(static_cast<int32_t*>(gend), K, status_p, static_cast<int32_t*>(dk),
@@ -479,8 +515,15 @@ int fit_common(int model, const surv_data* d, const surv_opts* o_in, double* bet
     int glaunches = 0;
     CUDA_TRY(survgpu::graph_init(P, s));
     ++launches;
-    CUDA_TRY(survgpu::run_ccd_graph(model, layout, prec, P, s, o_in && o_in->workspace ? &ws->graph : nullptr,
-                                    ev.a, &replays, &glaunches));
+    if (sn) {
+      CUDA_TRY(survgpu::sn_groups(static_cast<const int32_t*>(gend), K, n, const_cast<int32_t*>(S.grp), s));
+      ++launches;
+      CUDA_TRY(survgpu::run_sn_graph(P, S, s, o_in && o_in->workspace ? &ws->graph : nullptr, ev.a, &replays,
+                                     &glaunches));
+    } else {
+      CUDA_TRY(survgpu::run_ccd_graph(model, layout, prec, P, s, o_in && o_in->workspace ? &ws->graph : nullptr,
+                                      ev.a, &replays, &glaunches));
+    }
     launches += glaunches;
   } else {
     CUDA_TRY(cudaEventRecord(ev.a, s));

@@ -31,7 +31,7 @@
 #include <cstdlib>
 #include <cstring>
 
-#include "ccd_common.cuh"
+#include "graph_common.cuh"
 
 namespace survgpu {
 namespace {
@@ -53,36 +53,6 @@ struct GCfg {
 };
 constexpr int kTransThreads = 256;
 constexpr int kTransWarps = kTransThreads / 32;
-
-// Programmatic dependent launch: everything before pdl_wait() may only read
-// data that no earlier kernel of the fit writes.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" :::); }
-
-// Scalars of the control line a CTA reads (thread 0 loads them).
-struct LineView {
-  int stop = 0, nevals = 0;
-  double applied = 0.0;
-  ff delta = {0.f, 0.f};
-  double beta = 0.0, width = 0.0, pen = 0.0, dtx = 0.0, f_prev = 0.0;
-  long long passes = 0, eta_updates = 0;
-};
-__device__ __forceinline__ LineView load_line(const GraphCtl* ctl, int c) {
-  const CtlLine* L = &ctl->line[c % kRep];
-  LineView v;
-  v.stop = __ldcg(&L->stop);
-  v.nevals = __ldcg(&L->nevals);
-  v.applied = __ldcg(&L->applied);
-  v.delta = {__ldcg(&L->delta_hi), __ldcg(&L->delta_lo)};
-  v.beta = __ldcg(&L->beta);
-  v.width = __ldcg(&L->width);
-  v.pen = __ldcg(&L->pen);
-  v.dtx = __ldcg(&L->dtx);
-  v.f_prev = __ldcg(&L->f_prev);
-  v.passes = __ldcg(&L->passes);
-  v.eta_updates = __ldcg(&L->eta_updates);
-  return v;
-}
 
 // Per-fit parameters of a batched launch, read once per CTA into shared
 // memory (the table is written before the fit starts: it may be read before
@@ -115,6 +85,7 @@ __global__ void k_graph_init(const __grid_constant__ CcdParams P0) {
   L->f_prev = 0.0;
   L->passes = 0;
   L->eta_updates = 0;
+  L->dirty = 1;
 }
 
 // MULTI selects the group-end handling for warps that hold many ends (see
@@ -428,86 +399,9 @@ __global__ void __launch_bounds__(kTransThreads) k_trans(const __grid_constant__
     s_next[3] = P.dTx[jn];
   }
   __syncthreads();
-  if (w == 0) {
-    LineView out;
-    if (lane == 0) {
-      out = lv;
-      const double grad = lv.dtx - acc_to_d(s_red[0][0]);  // l' = delta^T X_j - sum_k d_k G_k
-      const double hess = -acc_to_d(s_red[0][1]);           // l''
-      out.passes = lv.passes + 1;
-      out.applied = 0.0;
-      out.delta = {0.f, 0.f};
-      if (eval) {
-        // objective at the start of sweep s = nevals and the stopping rule
-        const int sidx = lv.nevals;
-        const double ll = s_lin[0] - acc_to_d(s_red[0][2]);
-        const double f = ll + s_lin[1];
-        const double fp = sidx >= 1 ? lv.f_prev : 0.0;
-        const bool conv = sidx >= 1 && fabs(f - fp) / fabs(f) < P.tol;
-        out.stop = (conv || sidx >= P.max_sweeps) ? 1 : 0;
-        out.nevals = sidx + 1;
-        out.f_prev = f;
-        if (out.stop) {
-          P.out[OUT_LOGLIK] = ll;
-          P.out[OUT_OBJECTIVE] = f;
-          P.out[OUT_OBJECTIVE_PREV] = fp;
-          P.out[OUT_SWEEPS] = (double)sidx;
-          P.out[OUT_CONVERGED] = conv ? 1.0 : 0.0;
-          P.out[OUT_ETA_UPDATES] = (double)lv.eta_updates;
-          P.out[OUT_PASSES] = (double)out.passes;
-          ctl->done = 1;
-          if (P.done_count) atomicAdd(P.done_count, 1u);
-        }
-      }
-      double bnew = lv.beta, wnew = lv.width;
-      if (!out.stop) {
-        const double step = newton_step(lv.beta, grad, hess, P.penalty, lv.pen);
-        if (step != 0.0) out.applied = copysign(fmin(fabs(step), lv.width), step);
-        bnew = lv.beta + out.applied;
-        wnew = fmax(2.0 * fabs(out.applied), lv.width / 2.0);
-        P.beta[j] = bnew;
-        P.width[j] = wnew;
-        if (out.applied != 0.0) out.eta_updates = lv.eta_updates + 1;
-        out.delta = d_to_ff(out.applied);
-      }
-      if (P.p == 1) {
-        out.beta = bnew;
-        out.width = wnew;
-      } else {
-        out.beta = s_next[0];
-        out.width = s_next[1];
-      }
-      out.pen = s_next[2];
-      out.dtx = s_next[3];
-      ctl->ticket = 0u;
-    }
-    // every lane writes one replica of the line
-    out.stop = __shfl_sync(0xffffffffu, out.stop, 0);
-    out.nevals = __shfl_sync(0xffffffffu, out.nevals, 0);
-    out.applied = __shfl_sync(0xffffffffu, out.applied, 0);
-    out.delta.hi = __shfl_sync(0xffffffffu, out.delta.hi, 0);
-    out.delta.lo = __shfl_sync(0xffffffffu, out.delta.lo, 0);
-    out.beta = __shfl_sync(0xffffffffu, out.beta, 0);
-    out.width = __shfl_sync(0xffffffffu, out.width, 0);
-    out.pen = __shfl_sync(0xffffffffu, out.pen, 0);
-    out.dtx = __shfl_sync(0xffffffffu, out.dtx, 0);
-    out.f_prev = __shfl_sync(0xffffffffu, out.f_prev, 0);
-    out.passes = __shfl_sync(0xffffffffu, out.passes, 0);
-    out.eta_updates = __shfl_sync(0xffffffffu, out.eta_updates, 0);
-    CtlLine* L = &ctl->line[lane];
-    L->stop = out.stop;
-    L->nevals = out.nevals;
-    L->applied = out.applied;
-    L->delta_hi = out.delta.hi;
-    L->delta_lo = out.delta.lo;
-    L->beta = out.beta;
-    L->width = out.width;
-    L->pen = out.pen;
-    L->dtx = out.dtx;
-    L->f_prev = out.f_prev;
-    L->passes = out.passes;
-    L->eta_updates = out.eta_updates;
-  }
+  if (w == 0)
+    publish_step(P, j, lv, lv.dtx - acc_to_d(s_red[0][0]), -acc_to_d(s_red[0][1]), eval, s_lin[0],
+                 s_lin[1], acc_to_d(s_red[0][2]), s_next);
 }
 
 // Grid of the pass kernel: as many CTAs per SM (up to MINB) as fit.
@@ -644,6 +538,49 @@ cudaError_t time_one_sweep(int model, int layout, int prec, const CcdParams& P, 
   return cudaEventElapsedTime(ms, guard.a, guard.b);
 }
 
+cudaError_t graph_cache_prepare(GraphCache* gc) {
+  if (gc->cs) return cudaSuccess;
+  cudaError_t st;
+  if ((st = cudaStreamCreateWithFlags(&gc->cs, cudaStreamNonBlocking)) != cudaSuccess) return st;
+  for (auto& e : gc->ev)
+    if ((st = cudaEventCreateWithFlags(&e, cudaEventDisableTiming)) != cudaSuccess) return st;
+  return cudaMallocHost(&gc->flag, 2 * sizeof(int));
+}
+
+cudaError_t replay_until_stop(const CcdParams& P, cudaStream_t s, GraphCache* gc, cudaEvent_t t0,
+                              int launches_per_replay, int* replays, int* launches) {
+  cudaError_t st;
+  gc->flag[0] = gc->flag[1] = 0;
+  if (t0 && (st = cudaEventRecord(t0, s)) != cudaSuccess) return st;
+  // One replay per sweep.  The stop flag of replay i is read while replay
+  // i + 1 runs; kernels of a replay after the stop return at once.  The
+  // device stops at the evaluation of sweep max_sweeps at the latest, which
+  // falls in replay max_sweeps.  A batched launch ends when every fit has
+  // counted itself as stopped.
+  const int max_replays = P.max_sweeps + 2;
+  const int target = P.nfit > 0 ? P.nfit : 1;
+  const void* stop_src =
+      P.nfit > 0 ? static_cast<const void*>(P.done_count) : static_cast<const void*>(&P.gctl->done);
+  int i = 0;
+  for (; i < max_replays; ++i) {
+    if ((st = cudaGraphLaunch(gc->exec, s)) != cudaSuccess) return st;
+    *launches += launches_per_replay;
+    if ((st = cudaMemcpyAsync(gc->flag + (i & 1), stop_src, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+      return st;
+    if ((st = cudaEventRecord(gc->ev[i & 1], s)) != cudaSuccess) return st;
+    if (i >= 1) {
+      if ((st = cudaEventSynchronize(gc->ev[(i - 1) & 1])) != cudaSuccess) return st;
+      if (gc->flag[(i - 1) & 1] >= target) {
+        ++i;
+        break;
+      }
+    }
+  }
+  *replays = i;
+  // the last replay's flag copy must land before the host buffer is reused
+  return cudaEventSynchronize(gc->ev[(i - 1) & 1]);
+}
+
 cudaError_t run_ccd_graph(int model, int layout, int prec, const CcdParams& P, cudaStream_t s, GraphCache* gc,
                           cudaEvent_t t0, int* replays, int* launches) {
   *replays = 0;
@@ -655,12 +592,7 @@ cudaError_t run_ccd_graph(int model, int layout, int prec, const CcdParams& P, c
   } guard{gc ? nullptr : &local};
   if (!gc) gc = &local;
   cudaError_t st;
-  if (!gc->cs) {
-    if ((st = cudaStreamCreateWithFlags(&gc->cs, cudaStreamNonBlocking)) != cudaSuccess) return st;
-    for (auto& e : gc->ev)
-      if ((st = cudaEventCreateWithFlags(&e, cudaEventDisableTiming)) != cudaSuccess) return st;
-    if ((st = cudaMallocHost(&gc->flag, 2 * sizeof(int))) != cudaSuccess) return st;
-  }
+  if ((st = graph_cache_prepare(gc)) != cudaSuccess) return st;
   // programmatic dependent launch between the kernels; SURVGPU_GRAPH_PDL=0
   // turns it off (plain stream order), for comparison
   const char* env = std::getenv("SURVGPU_GRAPH_PDL");
@@ -683,35 +615,7 @@ cudaError_t run_ccd_graph(int model, int layout, int prec, const CcdParams& P, c
     gc->key = P;
     gc->mlp = mlp;
   }
-  gc->flag[0] = gc->flag[1] = 0;
-  if (t0 && (st = cudaEventRecord(t0, s)) != cudaSuccess) return st;
-  // One replay per sweep.  The stop flag of replay i is read while replay
-  // i + 1 runs; kernels of a replay after the stop return at once.  The
-  // device stops at the evaluation of sweep max_sweeps at the latest, which
-  // falls in replay max_sweeps.  A batched launch ends when every fit has
-  // counted itself as stopped.
-  const int max_replays = P.max_sweeps + 2;
-  const int target = P.nfit > 0 ? P.nfit : 1;
-  const void* stop_src =
-      P.nfit > 0 ? static_cast<const void*>(P.done_count) : static_cast<const void*>(&P.gctl->done);
-  int i = 0;
-  for (; i < max_replays; ++i) {
-    if ((st = cudaGraphLaunch(gc->exec, s)) != cudaSuccess) return st;
-    *launches += 2 * P.p;
-    if ((st = cudaMemcpyAsync(gc->flag + (i & 1), stop_src, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
-      return st;
-    if ((st = cudaEventRecord(gc->ev[i & 1], s)) != cudaSuccess) return st;
-    if (i >= 1) {
-      if ((st = cudaEventSynchronize(gc->ev[(i - 1) & 1])) != cudaSuccess) return st;
-      if (gc->flag[(i - 1) & 1] >= target) {
-        ++i;
-        break;
-      }
-    }
-  }
-  *replays = i;
-  // the last replay's flag copy must land before the host buffer is reused
-  return cudaEventSynchronize(gc->ev[(i - 1) & 1]);
+  return replay_until_stop(P, s, gc, t0, 2 * P.p, replays, launches);
 }
 
 }  // namespace survgpu

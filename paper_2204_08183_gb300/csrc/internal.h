@@ -106,7 +106,8 @@ struct alignas(128) CtlLine {
   double f_prev;         // objective at the latest evaluation
   long long passes;      // coordinate passes so far
   long long eta_updates; // nonzero steps so far
-  char pad[128 - 88];
+  int32_t dirty;         // sparse-numerator form: the risk-set sums are stale
+  char pad[128 - 92];
 };
 struct GraphCtl {
   CtlLine line[kRep];
@@ -166,6 +167,7 @@ cudaError_t ccd_grid_size(int model, int layout, int prec, int* G, int* wpc);
 struct GraphCache {
   cudaGraphExec_t exec = nullptr;
   CcdParams key;
+  unsigned char key2[256] = {};  // further launch parameters (sparse-numerator form)
   int mlp = -1;
   cudaStream_t cs = nullptr;     // capture stream
   cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -177,6 +179,36 @@ cudaError_t graph_init(const CcdParams& P, cudaStream_t s);
 cudaError_t run_ccd_graph(int model, int layout, int prec, const CcdParams& P, cudaStream_t s, GraphCache* gc,
                           cudaEvent_t t0, int* replays, int* launches);
 void graph_cache_free(GraphCache* gc);
+// Stream, events and pinned flags of a graph cache (idempotent).
+cudaError_t graph_cache_prepare(GraphCache* gc);
+// Replay gc->exec on s until the device reports the fit(s) stopped (at most
+// P.max_sweeps + 2 replays); t0 (optional) is recorded before the first.
+cudaError_t replay_until_stop(const CcdParams& P, cudaStream_t s, GraphCache* gc, cudaEvent_t t0,
+                              int launches_per_replay, int* replays, int* launches);
+
+// ---- sparse-numerator form (sn.cu; not in the paper) --------------------
+// Cox, CSC, FP32 mode.  Per coordinate, after a nonzero step only, the risk
+// sets are rebuilt (Den_k, Lambda, W); every coordinate's derivatives then
+// come from its nonzeros alone (O(nnz_j)).
+struct SnParams {
+  const int32_t* grp;    // [n] tie group of each subject
+  double* den;           // [K] Den_k
+  double* v1;            // [K] d_k / Den_k
+  double* v2;            // [K] d_k / Den_k^2
+  float2* lam;           // [K] Lambda(k) = sum_{k' >= k} d_k' / Den_k' (float-float)
+  float2* W;             // [K + 1] W(k) = sum_{k' < k} d_k' / Den_k'^2 (float-float)
+  double* part_den;      // [3][G] per-CTA sums of v1, v2 and d_k log Den_k
+  double* ll_den;        // [1] sum_k d_k log Den_k at the current e
+  uint64_t* part_col;    // [4][G2] per-CTA chunk totals of a = x e, S1, S2 and Q
+  int32_t G2;            // CTAs of the column kernels
+  int32_t multi;         // row pass for many group ends per warp
+};
+// Group of each subject from the group ends (prep).
+cudaError_t sn_groups(const int32_t* gend, int32_t K, int64_t n, int32_t* grp, cudaStream_t s);
+// Fit with the sparse-numerator kernels: graph_init(P) first, then replays
+// as run_ccd_graph.
+cudaError_t run_sn_graph(const CcdParams& P, const SnParams& S, cudaStream_t s, GraphCache* gc, cudaEvent_t t0,
+                         int* replays, int* launches);
 // One replay of the sweep graph of P (captured and destroyed here), timed
 // with events on s: *ms.  P's state must be initialised (graph_init).
 cudaError_t time_one_sweep(int model, int layout, int prec, const CcdParams& P, cudaStream_t s, float* ms);

@@ -23,6 +23,8 @@ struct surv_workspace {
     // cross-validated path (cox_cv_path) and lambda_max
     CV_FOLD, CV_DK, CV_DTX, CV_E, CV_ETA, CV_REC, CV_WT, CV_AGG, CV_PART, CV_GCTL, CV_BETA, CV_WIDTH, CV_PEN,
     CV_OUT, CV_FITS, CV_CTRL, CV_DEN, CV_HELD, CV_MEAN, LM_LAM, LM_R, LM_G,
+    // sparse-numerator form
+    SN_GRP, SN_DEN, SN_V1, SN_V2, SN_LAM, SN_W, SN_PDEN, SN_LL, SN_PCOL,
     NBUF
   };
   int device = -1;
