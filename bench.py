@@ -62,9 +62,10 @@ def parse():
     ap.add_argument("--cv-p", type=int, default=500, help="cv: covariates (500 = the benchmarked size; smaller "
                                                            "values give small cases for profiling)")
     ap.add_argument("--no-sequential", action="store_true", help="cv: skip the 200 sequential plain fits")
-    ap.add_argument("--schedule", choices=["graph", "persistent"], default="graph",
-                    help="graph: two kernels per coordinate replayed as a CUDA graph (default); "
-                         "persistent: one cooperative launch per fit")
+    ap.add_argument("--schedule", choices=["graph", "one", "persistent"], default="graph",
+                    help="graph: the default schedule (two kernels per row pass replayed as a CUDA graph, "
+                         "speculative batches of 4 coordinates per row pass); one: one coordinate per row "
+                         "pass (the paper's schedule); persistent: one cooperative launch per fit")
     return ap.parse_args()
 
 
@@ -170,6 +171,8 @@ def run_gpu(args, rank, world):
     flags = binding.SURV_FLAG_PERSISTENT if args.schedule == "persistent" else 0
     if sn:
         flags = binding.SURV_FLAG_SPARSE_NUMERATOR
+    if args.schedule == "one":
+        flags = binding.SURV_FLAG_ONE_COORDINATE
     kw = dict(penalty="l1", lam=lam, tol=1e-8, max_sweeps=1000, workspace=ws, flags=flags)
     beta_dev = torch.zeros(p, dtype=torch.float64, device="cuda")
     # the sampler starts before the warm-up so that its start-up cannot fall
@@ -223,6 +226,13 @@ def run_gpu(args, rank, world):
     per_pass = 4 * n + 8 * nnz / p + 8 * K          # e stream + column j (row, value) + group table
     per_update = 28 * nnz / p                         # row, value, eta r/w (8+8), e write
     alg_bytes = passes * per_pass + upd * per_update
+    row_passes = sum(i["row_passes"] for i in infos)
+    batched = (not sn) and args.schedule == "graph" and row_passes < passes
+    if batched:
+        # speculative batches: a row pass reads e once and the slices of up
+        # to 4 columns (counted as 4: an upper bound on the columns read)
+        per_row_pass = 4 * n + 4 * 8 * nnz / p + 8 * K
+        alg_bytes = row_passes * per_row_pass + upd * per_update
     if sn:
         # per coordinate: column j (row, value) and, per nonzero, e, its
         # group, Lambda and W (4 + 4 + 8 + 8); per rebuild of the risk sets
@@ -245,8 +255,13 @@ def run_gpu(args, rank, world):
                 "unit_of_work": "one coordinate (row pass + transform/Newton)",
                 "algorithmic_bytes_per_coordinate": round(alg_bytes / passes),
                 "us_per_coordinate": round(us_per_coord, 3),
-                "passes_per_fit": passes / len(infos), "eta_updates_per_fit": upd / len(infos)}
-    if args.schedule == "graph" and n == 10_000_000 and p == 100 and not sn:
+                "passes_per_fit": passes / len(infos), "eta_updates_per_fit": upd / len(infos),
+                "row_passes_per_fit": row_passes / len(infos)}
+    if batched:
+        roofline["unit_of_work"] = "one row pass (a speculative batch of up to 4 coordinates)"
+        roofline["algorithmic_bytes_per_row_pass"] = round(alg_bytes / row_passes)
+        roofline["us_per_row_pass"] = round(kern_ms * 1e3 / row_passes, 3)
+    if args.schedule == "one" and n == 10_000_000 and p == 100 and not sn:
         # dram__bytes_read.sum + dram__bytes_write.sum of k_pass + k_trans per
         # coordinate, steady state (ncu --cache-control none, one pass); see
         # profiles/k_pass_k_trans_cox_csc_n1e7.md.  e stays in L2 across
@@ -257,6 +272,9 @@ def run_gpu(args, rank, world):
         roofline["traffic"] = None
     roofline["kernel"] = ("ccd_kernel<cox,csc,f32> (persistent, one launch per fit)" if args.schedule == "persistent"
                           else "k_pass + k_trans <cox,csc,f32>, one pair per coordinate, one graph replay per sweep")
+    if batched:
+        roofline["kernel"] = ("k_spass<4> + k_strans<4>: one pair per speculative batch of 4 coordinates, "
+                              "graph replays of batches")
     if sn:
         roofline["kernel"] = ("k_sn_den_a/den_b/lam (after nonzero steps only) + k_sn_col_a/col_b per coordinate, "
                               "one graph replay per sweep")
@@ -276,6 +294,7 @@ def run_gpu(args, rank, world):
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": config_dict(n, p, lam), "roofline": roofline, "clocks": clk, "gpu_launches": launches,
            "fit": {"sweeps_per_fit": infos[-1]["sweeps"], "converged": infos[-1]["converged"],
+                   "row_passes_per_fit": infos[-1]["row_passes"],
                    "nnz_beta": infos[-1]["nnz_beta"], "loglik": infos[-1]["loglik"], "n_groups": K,
                    "ms_per_fit": round(t_max / args.steps, 3)}}
 

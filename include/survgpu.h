@@ -142,6 +142,15 @@ typedef struct surv_opts {
  * coordinate whose step is zero costs O(nnz_j).  Its speed is reported
  * separately from the paper's method. */
 #define SURV_FLAG_SPARSE_NUMERATOR 8
+/* Cox fits of CSC data in the FP32 mode run speculative coordinate batches
+ * by default: one row pass evaluates the derivatives of 4 consecutive
+ * coordinates at the same e; their steps are taken in order up to and
+ * including the first nonzero one (e is unchanged before it, so each step is
+ * the one cyclic CCD takes, from the same sums) and the next pass starts
+ * after it.  (Fits whose tie groups outnumber twice the warps of the grid
+ * take one coordinate per pass.)  This flag turns the batches off: one
+ * coordinate per row pass, as the paper's schedule. */
+#define SURV_FLAG_ONE_COORDINATE 16
 
 /* Fill *opts with defaults: no penalty, FP32-compensated precision,
  * tol 1e-8, max_sweeps 1000, default stream, no workspace. */
@@ -170,6 +179,8 @@ typedef struct surv_fit_info {
                                     dense [12] and sparse [13] part of the
                                     pass; CTA 0 exchange-1 warp sums [14] and
                                     payload stores [15] (inside [1])        */
+  int64_t row_passes;            /* passes over the subjects run: one per
+                                    coordinate, fewer with speculative batches */
 } surv_fit_info;
 
 /* ---- entry points ------------------------------------------------------ */

@@ -40,6 +40,7 @@ SURV_FLAG_TEST_STALL = 1
 SURV_FLAG_PERSISTENT = 2
 SURV_FLAG_CV_TUNE = 4
 SURV_FLAG_SPARSE_NUMERATOR = 8
+SURV_FLAG_ONE_COORDINATE = 16
 
 # exported symbols, in the order the header declares them
 EXPORTS = ["surv_opts_default", "surv_workspace_create", "surv_workspace_destroy", "surv_sort_desc",
@@ -71,7 +72,7 @@ class surv_fit_info(C.Structure):
                 ("device_error", C.c_int32), ("loglik", C.c_double), ("objective", C.c_double),
                 ("objective_prev", C.c_double), ("n_groups", C.c_int64), ("coordinate_passes", C.c_int64),
                 ("eta_updates", C.c_int64), ("kernel_launches", C.c_int64), ("ccd_kernel_ms", C.c_double),
-                ("phase_ms", C.c_double * 16)]
+                ("phase_ms", C.c_double * 16), ("row_passes", C.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

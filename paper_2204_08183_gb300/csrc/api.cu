@@ -266,7 +266,11 @@ int fit_common(int model, const surv_data* d, const surv_opts* o_in, double* bet
   if (d->dtype != SURV_F32 && d->dtype != SURV_F64) { set_error("bad dtype"); return SURV_E_INVALID; }
   if (o.penalty < 0 || o.penalty > 2 || o.precision < 0 || o.precision > 1) { set_error("bad penalty/precision"); return SURV_E_INVALID; }
   if (!(o.lambda >= 0.0) || !std::isfinite(o.lambda) || !(o.tol >= 0.0) || o.max_sweeps < 0) { set_error("bad lambda/tol/max_sweeps"); return SURV_E_INVALID; }
-  if ((o.flags & ~(SURV_FLAG_TEST_STALL | SURV_FLAG_PERSISTENT | SURV_FLAG_SPARSE_NUMERATOR)) != 0) { set_error("unknown flags"); return SURV_E_INVALID; }
+  if ((o.flags & ~(SURV_FLAG_TEST_STALL | SURV_FLAG_PERSISTENT | SURV_FLAG_SPARSE_NUMERATOR | SURV_FLAG_ONE_COORDINATE)) !=
+      0) {
+    set_error("unknown flags");
+    return SURV_E_INVALID;
+  }
   // the sparse-numerator form: Cox, CSC, FP32 mode, a full fit on the default schedule
   const bool sn = (o.flags & SURV_FLAG_SPARSE_NUMERATOR) != 0;
   if (sn && (model != SURV_COX || d->layout != SURV_CSC || o.precision != SURV_PREC_F32C || single_j >= 0 ||
@@ -349,7 +353,17 @@ int fit_common(int model, const surv_data* d, const surv_opts* o_in, double* bet
   if ((rc = ensure(ws, W::GK, 8 * (size_t)K, &Gk))) return rc;
   void* Gkff = nullptr;
   if ((rc = ensure(ws, W::GKFF, 8 * (size_t)K, &Gkff))) return rc;
-  if ((rc = ensure(ws, W::REC, accsz * (size_t)K * M, &rec))) return rc;
+  // speculative coordinate batches (the default for Cox fits of CSC data in
+  // the FP32 mode with few tie groups per warp): 4 columns per row pass, the
+  // fastest measured at N = 10^7 (8 columns: SURVGPU_SPEC_B=8, for comparison)
+  int spec_b = 0;
+  if (!(o.flags & SURV_FLAG_ONE_COORDINATE) && graph && !sn && model == SURV_COX && layout == SURV_CSC &&
+      prec == 0 && p >= 2 && (int64_t)K < 2 * (int64_t)nwarps) {
+    const char* eb = std::getenv("SURVGPU_SPEC_B");
+    spec_b = (eb && eb[0] == '8') ? 8 : 4;
+  }
+  const int R = spec_b ? 1 + 2 * spec_b : M;  // record / aggregate components
+  if ((rc = ensure(ws, W::REC, accsz * (size_t)K * R, &rec))) return rc;
   if ((rc = ensure(ws, W::E, tsz * (size_t)n, &e))) return rc;
   if ((rc = ensure(ws, W::ETA, 8 * (size_t)n, &eta))) return rc;
   if (model == SURV_FG && (rc = ensure(ws, W::W2, tsz * (size_t)n, &w2))) return rc;
@@ -363,8 +377,8 @@ int fit_common(int model, const surv_data* d, const surv_opts* o_in, double* bet
   if ((rc = ensure(ws, W::SLOTS, 2 * slot_bytes, &slots))) return rc;
   void* wt = nullptr;
   void* aggr = nullptr;
-  if (graph && (rc = ensure(ws, W::WT, 8 * (size_t)M * nwarps, &wt))) return rc;
-  if (graph && (rc = ensure(ws, W::AGG, 8 * (size_t)survgpu::kRep * M * G, &aggr))) return rc;
+  if (graph && (rc = ensure(ws, W::WT, 8 * (size_t)R * nwarps, &wt))) return rc;
+  if (graph && (rc = ensure(ws, W::AGG, 8 * (size_t)survgpu::kRep * R * G, &aggr))) return rc;
   survgpu::SnParams S;
   std::memset(&S, 0, sizeof(S));
   if (sn) {
@@ -515,7 +529,10 @@ int fit_common(int model, const surv_data* d, const surv_opts* o_in, double* bet
     int glaunches = 0;
     CUDA_TRY(survgpu::graph_init(P, s));
     ++launches;
-    if (sn) {
+    if (spec_b) {
+      CUDA_TRY(survgpu::run_spec_graph(P, spec_b, s, o_in && o_in->workspace ? &ws->graph : nullptr, ev.a, &replays,
+                                       &glaunches));
+    } else if (sn) {
       CUDA_TRY(survgpu::sn_groups(static_cast<const int32_t*>(gend), K, n, const_cast<int32_t*>(S.grp), s));
       ++launches;
       CUDA_TRY(survgpu::run_sn_graph(P, S, s, o_in && o_in->workspace ? &ws->graph : nullptr, ev.a, &replays,
@@ -560,6 +577,7 @@ int fit_common(int model, const surv_data* d, const surv_opts* o_in, double* bet
     info->ccd_kernel_ms = kernel_ms;
     for (int i = 0; i < 16; ++i) info->phase_ms[i] = (double)hc.timing[i] * 1e-6;
     info->phase_ms[survgpu::PH_PASS_SUM] /= (double)G;  // mean over CTAs
+    info->row_passes = (int64_t)hc.out[spec_b ? survgpu::OUT_BATCHES : survgpu::OUT_PASSES];
   }
   if (graph && hc.gctl.done != 1) {
     set_error("CCD stopped after %d sweep replays without a stop decision", replays);

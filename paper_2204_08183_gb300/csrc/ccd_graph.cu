@@ -86,6 +86,9 @@ __global__ void k_graph_init(const __grid_constant__ CcdParams P0) {
   L->passes = 0;
   L->eta_updates = 0;
   L->dirty = 1;
+  L->j0 = 0;
+  L->q = -1;
+  L->batches = 0;
 }
 
 // MULTI selects the group-end handling for warps that hold many ends (see
@@ -548,7 +551,7 @@ cudaError_t graph_cache_prepare(GraphCache* gc) {
 }
 
 cudaError_t replay_until_stop(const CcdParams& P, cudaStream_t s, GraphCache* gc, cudaEvent_t t0,
-                              int launches_per_replay, int* replays, int* launches) {
+                              int launches_per_replay, int* replays, int* launches, int max_replays_in) {
   cudaError_t st;
   gc->flag[0] = gc->flag[1] = 0;
   if (t0 && (st = cudaEventRecord(t0, s)) != cudaSuccess) return st;
@@ -557,7 +560,7 @@ cudaError_t replay_until_stop(const CcdParams& P, cudaStream_t s, GraphCache* gc
   // device stops at the evaluation of sweep max_sweeps at the latest, which
   // falls in replay max_sweeps.  A batched launch ends when every fit has
   // counted itself as stopped.
-  const int max_replays = P.max_sweeps + 2;
+  const int max_replays = max_replays_in > 0 ? max_replays_in : P.max_sweeps + 2;
   const int target = P.nfit > 0 ? P.nfit : 1;
   const void* stop_src =
       P.nfit > 0 ? static_cast<const void*>(P.done_count) : static_cast<const void*>(&P.gctl->done);

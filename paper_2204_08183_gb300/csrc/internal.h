@@ -107,7 +107,10 @@ struct alignas(128) CtlLine {
   long long passes;      // coordinate passes so far
   long long eta_updates; // nonzero steps so far
   int32_t dirty;         // sparse-numerator form: the risk-set sums are stale
-  char pad[128 - 92];
+  int32_t j0;            // speculative batches: first coordinate of the next batch
+  int32_t q;             //   and the coordinate whose step is still to be applied (-1: none)
+  long long batches;     //   and the row passes so far
+  char pad[128 - 112];
 };
 struct GraphCtl {
   CtlLine line[kRep];
@@ -148,6 +151,7 @@ enum OutIndex : int {
   OUT_HESS = 7,
   OUT_PASSES = 8,
   OUT_EPOCH_END = 9,
+  OUT_BATCHES = 10,     // row passes of the speculative-batch schedule
   OUT_COUNT = 16,
 };
 
@@ -184,7 +188,15 @@ cudaError_t graph_cache_prepare(GraphCache* gc);
 // Replay gc->exec on s until the device reports the fit(s) stopped (at most
 // P.max_sweeps + 2 replays); t0 (optional) is recorded before the first.
 cudaError_t replay_until_stop(const CcdParams& P, cudaStream_t s, GraphCache* gc, cudaEvent_t t0,
-                              int launches_per_replay, int* replays, int* launches);
+                              int launches_per_replay, int* replays, int* launches, int max_replays = 0);
+
+// ---- speculative coordinate batches (spec.cu) ----------------------------
+// Cox, CSC, FP32 mode: each row pass evaluates the derivatives of B
+// consecutive coordinates at the same e; the steps are taken in order up to
+// the first nonzero one (e is unchanged before it, so every committed step
+// is the one cyclic CCD takes).  graph_init(P) first.
+cudaError_t run_spec_graph(const CcdParams& P, int B, cudaStream_t s, GraphCache* gc, cudaEvent_t t0, int* replays,
+                           int* launches);
 
 // ---- sparse-numerator form (sn.cu; not in the paper) --------------------
 // Cox, CSC, FP32 mode.  Per coordinate, after a nonzero step only, the risk

@@ -141,7 +141,19 @@ __global__ void k_group_stats(const int32_t* gend, int32_t K, const int8_t* stat
   for (int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; k < K; k += nwarp) {
   const int64_t a = k == 0 ? 0 : (int64_t)gend[k - 1] + 1, b = gend[k];
   int d = 0, c = 0;
-  for (int64_t i = a + lane; i <= b; i += 32) {
+  // eight independent loads in flight per lane
+  int64_t i = a + lane;
+  for (; i + 7 * 32 <= b; i += 8 * 32) {
+    int sv[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) sv[u] = status[i + 32 * u];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      d += sv[u] == 1;
+      c += sv[u] == 0;
+    }
+  }
+  for (; i <= b; i += 32) {
     const int s = status[i];
     d += s == 1;
     c += s == 0;
@@ -210,9 +222,27 @@ __global__ void k_dtx_csc(const int64_t* col_ptr, const int32_t* row_idx, const 
   using A = typename AccOf<T>::type;
   const int64_t j = blockIdx.x;
   const int64_t a = col_ptr[j], b = col_ptr[j + 1];
+  const int64_t NT = blockDim.x;
   A acc;
   acc_zero(acc);
-  for (int64_t i = a + threadIdx.x; i < b; i += blockDim.x)
+  // eight independent gathers in flight per thread
+  int64_t i = a + threadIdx.x;
+  for (; i + 7 * NT < b; i += 8 * NT) {
+    int32_t r[8];
+    T v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      r[u] = row_idx[i + u * NT];
+      v[u] = values ? values[i + u * NT] : T(1);
+    }
+    int8_t st[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) st[u] = status[r[u]];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (st[u] == 1) acc = acc_add_v(acc, v[u]);
+  }
+  for (; i < b; i += NT)
     if (status[row_idx[i]] == 1) acc = acc_add_v(acc, values ? values[i] : T(1));
   block_sum_store<T>(acc, dTx + j);
 }
@@ -426,9 +456,9 @@ cudaError_t prep_dtx_csc(const int64_t* col_ptr, const int32_t* row_idx, const v
                          const int8_t* status, int64_t p, double* dTx, cudaStream_t s) {
   if (p <= 0) return cudaSuccess;
   if (prec == 0)
-    k_dtx_csc<float><<<(unsigned)p, kPrepThreads, 0, s>>>(col_ptr, row_idx, (const float*)values, status, dTx);
+    k_dtx_csc<float><<<(unsigned)p, 1024, 0, s>>>(col_ptr, row_idx, (const float*)values, status, dTx);
   else
-    k_dtx_csc<double><<<(unsigned)p, kPrepThreads, 0, s>>>(col_ptr, row_idx, (const double*)values, status, dTx);
+    k_dtx_csc<double><<<(unsigned)p, 1024, 0, s>>>(col_ptr, row_idx, (const double*)values, status, dTx);
   return cudaGetLastError();
 }
 

@@ -75,6 +75,7 @@ int main(void) {
   F(surv_fit_info, device_error); F(surv_fit_info, loglik); F(surv_fit_info, objective);
   F(surv_fit_info, objective_prev); F(surv_fit_info, n_groups); F(surv_fit_info, coordinate_passes);
   F(surv_fit_info, eta_updates); F(surv_fit_info, kernel_launches); F(surv_fit_info, ccd_kernel_ms); F(surv_fit_info, phase_ms);
+  F(surv_fit_info, row_passes);
   return 0;
 }
 ''')

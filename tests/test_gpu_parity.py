@@ -152,7 +152,9 @@ def test_deterministic(lib):
 
 
 # ------------------------------------------------------------ full fits
-SCHEDULES = {"graph": 0, "persistent": binding.SURV_FLAG_PERSISTENT}
+# graph: the default (speculative batches for Cox CSC FP32 fits); one: one
+# coordinate per row pass; persistent: one cooperative launch per fit
+SCHEDULES = {"graph": 0, "one": binding.SURV_FLAG_ONE_COORDINATE, "persistent": binding.SURV_FLAG_PERSISTENT}
 
 
 def _fit_check(model, d, penalty, lam, prec, beta_tol=1e-5, tol=1e-10, where="device", schedule="graph"):
@@ -187,7 +189,7 @@ def test_fit_dense_cox_l2_config1_shape(lib, prec):
     _fit_check("cox", d, "l2", 1.0, prec, tol=1e-8)
 
 
-@pytest.mark.parametrize("schedule", ["graph", "persistent"])
+@pytest.mark.parametrize("schedule", ["graph", "one", "persistent"])
 @pytest.mark.parametrize("prec", ["f32c", "f64"])
 def test_fit_csc_cox_l1(lib, prec, schedule):
     d = synth.cohort_cox_sparse(60_000, 20, seed=2, density=0.05, n_true=4, laplace_scale=0.5, grid=3650)

@@ -42,8 +42,10 @@ def test_sn_fit_matches_oracle_l2(lib):
 def test_sn_equals_row_pass_fit(lib):
     d = small_csc(50000, 20, seed=9, density=0.05, n_times=1000, binary=True)
     sd = survdata(d)
-    b0, i0, _ = binding.cox_fit(sd, penalty="l1", lam=20.0, tol=1e-10)
-    b1, i1, _ = binding.cox_fit(sd, penalty="l1", lam=20.0, tol=1e-10, flags=SN)
+    # tolerance 1e-7: the FP32 mode's objective carries rounding noise near
+    # 1e-11 relative, which would decide the sweep count at tighter ones
+    b0, i0, _ = binding.cox_fit(sd, penalty="l1", lam=20.0, tol=1e-7)
+    b1, i1, _ = binding.cox_fit(sd, penalty="l1", lam=20.0, tol=1e-7, flags=SN)
     assert i0["sweeps"] == i1["sweeps"]
     np.testing.assert_allclose(b1, b0, rtol=0, atol=1e-6)
     assert i1["loglik"] == pytest.approx(i0["loglik"], rel=1e-9)
@@ -94,7 +96,7 @@ def test_sn_long_column(lib):
     # column kernels take more CTAs
     d = small_csc(2_000_000, 3, seed=13, density=0.5, n_times=5000, binary=True)
     sd = survdata(d)
-    b0, i0, _ = binding.cox_fit(sd, penalty="l2", lam=5.0, tol=1e-10)
-    b1, i1, _ = binding.cox_fit(sd, penalty="l2", lam=5.0, tol=1e-10, flags=SN)
+    b0, i0, _ = binding.cox_fit(sd, penalty="l2", lam=5.0, tol=1e-7)
+    b1, i1, _ = binding.cox_fit(sd, penalty="l2", lam=5.0, tol=1e-7, flags=SN)
     assert i1["sweeps"] == i0["sweeps"]
     np.testing.assert_allclose(b1, b0, rtol=0, atol=1e-6)
