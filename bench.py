@@ -259,9 +259,17 @@ def run_gpu(args, rank, world):
                 "row_passes_per_fit": row_passes / len(infos)}
     if batched:
         roofline["unit_of_work"] = "one row pass (a speculative batch of up to 4 coordinates)"
+        if n == 10_000_000 and p == 100:
+            # dram__bytes_read.sum + dram__bytes_write.sum of k_spass<4> +
+            # k_strans<4> per row pass, steady state (ncu --cache-control
+            # none); see profiles/k_spass_k_strans_cox_csc_n1e7.md
+            roofline["traffic"] = round((21353933 + 4378931) + (10547 + 38246))
+            roofline["traffic_note"] = "bytes per row pass, ncu steady-state capture of the kernels as committed"
         roofline["algorithmic_bytes_per_row_pass"] = round(alg_bytes / row_passes)
         roofline["us_per_row_pass"] = round(kern_ms * 1e3 / row_passes, 3)
-    if args.schedule == "one" and n == 10_000_000 and p == 100 and not sn:
+    if batched:
+        roofline.setdefault("traffic", None)
+    elif args.schedule == "one" and n == 10_000_000 and p == 100 and not sn:
         # dram__bytes_read.sum + dram__bytes_write.sum of k_pass + k_trans per
         # coordinate, steady state (ncu --cache-control none, one pass); see
         # profiles/k_pass_k_trans_cox_csc_n1e7.md.  e stays in L2 across
