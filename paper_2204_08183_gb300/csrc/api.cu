@@ -354,8 +354,11 @@ int fit_common(int model, const surv_data* d, const surv_opts* o_in, double* bet
   void* Gkff = nullptr;
   if ((rc = ensure(ws, W::GKFF, 8 * (size_t)K, &Gkff))) return rc;
   // speculative coordinate batches (the default for Cox fits of CSC data in
-  // the FP32 mode with few tie groups per warp): 4 columns per row pass, the
-  // fastest measured at N = 10^7 (8 columns: SURVGPU_SPEC_B=8, for comparison)
+  // the FP32 mode): 4 columns per row pass, the fastest measured at N = 10^7
+  // (8 columns: SURVGPU_SPEC_B=8, for comparison).  Not when the tie groups
+  // outnumber twice the warps: the transform of 4 columns at ~10^6 group
+  // ends costs more than the passes saved (measured 107 against 68 ms per
+  // fit at N = 2 x 10^6 with unique times).
   int spec_b = 0;
   if (!(o.flags & SURV_FLAG_ONE_COORDINATE) && graph && !sn && model == SURV_COX && layout == SURV_CSC &&
       prec == 0 && p >= 2 && (int64_t)K < 2 * (int64_t)nwarps) {
@@ -758,10 +761,14 @@ int cv_impl(const surv_data* d, const int8_t* fold_id, int nfolds, const double*
   // shared tables, per-fold tables, per-fit state (scratch sized for the
   // largest grid tried)
   const int32_t nwarps_alloc = Galloc * wpc;
+  // one coordinate per pass: the fits run in lockstep, so speculative
+  // batches would be as many as the slowest fit needs (measured slower:
+  // 180 against 237 fits/s at N = 10^6, 200 fits)
+  const int RC = M, NPART = 3;
   void *gend, *dk, *ck, *wk0, *woff = nullptr, *dkf, *dtxf, *cvc_v;
   void *e, *eta, *rec, *wt, *agg, *part, *gctl, *beta, *width, *pen, *out, *fits, *den, *held, *mean;
-  const size_t rec_f = pad((size_t)K * M, 8), wt_f = pad((size_t)M * nwarps_alloc, 8);
-  const size_t agg_f = pad((size_t)survgpu::kRep * M * Galloc, 8), part_f = pad((size_t)3 * Galloc, 8);
+  const size_t rec_f = pad((size_t)K * RC, 8), wt_f = pad((size_t)RC * nwarps_alloc, 8);
+  const size_t agg_f = pad((size_t)survgpu::kRep * RC * Galloc, 8), part_f = pad((size_t)NPART * Galloc, 8);
   if ((rc = ensure(ws, W::GEND, 4 * (size_t)K, &gend))) return rc;
   if ((rc = ensure(ws, W::DK, 4 * (size_t)K, &dk))) return rc;
   if ((rc = ensure(ws, W::CK, 4 * (size_t)K, &ck))) return rc;

@@ -54,18 +54,6 @@ struct GCfg {
 constexpr int kTransThreads = 256;
 constexpr int kTransWarps = kTransThreads / 32;
 
-// Per-fit parameters of a batched launch, read once per CTA into shared
-// memory (the table is written before the fit starts: it may be read before
-// the wait on the previous kernel).
-__device__ __forceinline__ void load_fit(CcdParams& dst, const CcdParams& P0) {
-  static_assert(sizeof(CcdParams) % 8 == 0, "CcdParams is copied in 8-byte words");
-  constexpr int W = sizeof(CcdParams) / 8;
-  const unsigned long long* src = reinterpret_cast<const unsigned long long*>(P0.fits + blockIdx.y);
-  unsigned long long* d = reinterpret_cast<unsigned long long*>(&dst);
-  for (int i = threadIdx.x; i < W; i += blockDim.x) d[i] = __ldg(src + i);
-  __syncthreads();
-}
-
 // Fill every control line for the first coordinate of a fit (of fit
 // blockIdx.y in a batched launch).
 __global__ void k_graph_init(const __grid_constant__ CcdParams P0) {

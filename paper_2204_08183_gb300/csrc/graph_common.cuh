@@ -38,6 +38,18 @@ __device__ __forceinline__ LineView load_line(const GraphCtl* ctl, int c) {
   return v;
 }
 
+// Per-fit parameters of a batched launch, read once per CTA into shared
+// memory (the table is written before the fit starts: it may be read before
+// the wait on the previous kernel).
+__device__ __forceinline__ void load_fit(CcdParams& dst, const CcdParams& P0) {
+  static_assert(sizeof(CcdParams) % 8 == 0, "CcdParams is copied in 8-byte words");
+  constexpr int W = sizeof(CcdParams) / 8;
+  const unsigned long long* src = reinterpret_cast<const unsigned long long*>(P0.fits + blockIdx.y);
+  unsigned long long* d = reinterpret_cast<unsigned long long*>(&dst);
+  for (int i = threadIdx.x; i < W; i += blockDim.x) d[i] = __ldg(src + i);
+  __syncthreads();
+}
+
 // The step of coordinate j, taken by warp 0 of the kernel's last CTA
 // (Section 2.4): lane 0 gets l' (grad) and l'' (hess); on an evaluation pass
 // (eval, j = 0) the objective f = lin - sum_dlog + pen at the start of the

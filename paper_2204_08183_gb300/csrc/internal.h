@@ -197,6 +197,8 @@ cudaError_t replay_until_stop(const CcdParams& P, cudaStream_t s, GraphCache* gc
 // is the one cyclic CCD takes).  graph_init(P) first.
 cudaError_t run_spec_graph(const CcdParams& P, int B, cudaStream_t s, GraphCache* gc, cudaEvent_t t0, int* replays,
                            int* launches);
+// Batches per graph replay.
+int spec_slots(int p, int B);
 
 // ---- sparse-numerator form (sn.cu; not in the paper) --------------------
 // Cox, CSC, FP32 mode.  Per coordinate, after a nonzero step only, the risk

@@ -478,7 +478,16 @@ cudaError_t capture_spec(const CcdParams& P, int S, bool pdl, cudaStream_t cs, c
   return lst != cudaSuccess ? lst : st;
 }
 
+// the kernels for B columns a batch (one fit)
+cudaError_t capture_any_spec(const CcdParams& P, int B, int S, bool pdl, cudaStream_t cs, cudaGraph_t* g) {
+  if (P.nfit > 0) return cudaErrorInvalidValue;
+  return B == 4 ? capture_spec<4>(P, S, pdl, cs, g) : capture_spec<8>(P, S, pdl, cs, g);
+}
+
 }  // namespace
+
+// Slots (batches) per graph replay for p coordinates and B columns a batch.
+int spec_slots(int p, int B) { return std::max(8, (p + B - 1) / B + 2); }
 
 cudaError_t run_spec_graph(const CcdParams& P, int B, cudaStream_t s, GraphCache* gc, cudaEvent_t t0, int* replays,
                            int* launches) {
@@ -496,7 +505,7 @@ cudaError_t run_spec_graph(const CcdParams& P, int B, cudaStream_t s, GraphCache
   const char* env = std::getenv("SURVGPU_GRAPH_PDL");
   const bool pdl = !(env && env[0] == '0');
   // batches per replay: about one sweep's worth when half the steps are zero
-  const int S = std::max(8, (P.p + B - 1) / B + 2);
+  const int S = spec_slots(P.p, B);
   const int mlp = 2000 + B * 2 + (pdl ? 1 : 0);
   if (!gc->exec || gc->mlp != mlp || std::memcmp(&gc->key, &P, sizeof(P)) != 0) {
     if (gc->exec) {
@@ -504,7 +513,7 @@ cudaError_t run_spec_graph(const CcdParams& P, int B, cudaStream_t s, GraphCache
       gc->exec = nullptr;
     }
     cudaGraph_t g = nullptr;
-    st = B == 4 ? capture_spec<4>(P, S, pdl, gc->cs, &g) : capture_spec<8>(P, S, pdl, gc->cs, &g);
+    st = capture_any_spec(P, B, S, pdl, gc->cs, &g);
     if (st == cudaSuccess) st = cudaGraphInstantiate(&gc->exec, g, 0);
     if (g) cudaGraphDestroy(g);
     if (st != cudaSuccess) {
