@@ -413,7 +413,7 @@ int fit_common(int model, const surv_data* d, const surv_opts* o_in, double* bet
   }
 
   CUDA_TRY(survgpu::prep_write_ends(time_p, n, static_cast<const int32_t*>(blockcnt), static_cast<int32_t*>(gend), s));
-  CUDA_TRY(survgpu::prep_group_stats(static_cast<int32_t*>(gend), K, status_p, static_cast<int32_t*>(dk),
+  CUDA_TRY(survgpu::prep_group_stats(static_cast<int32_t*>(gend), K, status_p, n, static_cast<int32_t*>(dk),
                                      static_cast<int32_t*>(ck), &ctrl->total_events, s));
   launches += 2;
   if (model == SURV_FG) {
@@ -640,7 +640,7 @@ int lambda_max_impl(const surv_data* d, const double* pf_in, double* out, void* 
   if ((rc = ensure(&ws, W::LM_R, 8 * (size_t)n, &r))) return rc;
   if ((rc = ensure(&ws, W::LM_G, 8 * (size_t)(p + 1), &g))) return rc;
   CUDA_TRY(survgpu::prep_write_ends(stg.time, n, static_cast<const int32_t*>(blockcnt), static_cast<int32_t*>(gend), s));
-  CUDA_TRY(survgpu::prep_group_stats(static_cast<int32_t*>(gend), K, stg.status, static_cast<int32_t*>(dk),
+  CUDA_TRY(survgpu::prep_group_stats(static_cast<int32_t*>(gend), K, stg.status, n, static_cast<int32_t*>(dk),
                                      static_cast<int32_t*>(ck), &ctrl->total_events, s));
   double* gd = static_cast<double*>(g);
   CUDA_TRY(survgpu::lambda_max_device(layout, prec, stg.colptr, stg.rowidx, stg.vals, stg.ld, n, p, stg.status,
@@ -797,7 +797,7 @@ int cv_impl(const surv_data* d, const int8_t* fold_id, int nfolds, const double*
   CUDA_TRY(cudaMemsetAsync(cvc, 0, sizeof(CvCtrl), s));
   CUDA_TRY(survgpu::cv_check_folds(fold_d, n, nfolds, &cvc->perr, s));
   CUDA_TRY(survgpu::prep_write_ends(stg.time, n, static_cast<const int32_t*>(blockcnt), static_cast<int32_t*>(gend), s));
-  CUDA_TRY(survgpu::prep_group_stats(static_cast<int32_t*>(gend), K, stg.status, static_cast<int32_t*>(dk),
+  CUDA_TRY(survgpu::prep_group_stats(static_cast<int32_t*>(gend), K, stg.status, n, static_cast<int32_t*>(dk),
                                      static_cast<int32_t*>(ck), &ctrl->total_events, s));
   CUDA_TRY(survgpu::cv_fold_stats(static_cast<int32_t*>(gend), K, stg.status, fold_d, nfolds,
                                   static_cast<int32_t*>(dkf), cvc->events, s));
@@ -1090,7 +1090,7 @@ int surv_groups(const int32_t* time, const int8_t* status, int64_t n, int64_t ma
   if ((rc = ensure(&ws, W::CK, 4 * (size_t)K, &ck))) return rc;
   if ((rc = ensure(&ws, W::GK, 8 * (size_t)K, &Gk))) return rc;
   CUDA_TRY(survgpu::prep_write_ends(tp, n, static_cast<const int32_t*>(blockcnt), static_cast<int32_t*>(gend), s));
-  CUDA_TRY(survgpu::prep_group_stats(static_cast<int32_t*>(gend), K, sp, static_cast<int32_t*>(dk),
+  CUDA_TRY(survgpu::prep_group_stats(static_cast<int32_t*>(gend), K, sp, n, static_cast<int32_t*>(dk),
                                      static_cast<int32_t*>(ck), &ctrl->total_events, s));
   CUDA_TRY(survgpu::prep_km(static_cast<int32_t*>(gend), static_cast<int32_t*>(ck), K, static_cast<double*>(Gk), nullptr, s));
   if (gend_out) CUDA_TRY(cudaMemcpyAsync(gend_out, gend, 4 * (size_t)K, cudaMemcpyDefault, s));

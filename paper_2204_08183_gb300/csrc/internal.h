@@ -239,8 +239,10 @@ cudaError_t prep_check_finite_f64(const double* v, int64_t count, unsigned* perr
 int64_t prep_end_blocks(int64_t n);
 cudaError_t prep_count_ends(const int32_t* time, int64_t n, int32_t* blockcnt, int32_t* K_dev, cudaStream_t s);
 cudaError_t prep_write_ends(const int32_t* time, int64_t n, const int32_t* blockoff, int32_t* gend, cudaStream_t s);
-cudaError_t prep_group_stats(const int32_t* gend, int32_t K, const int8_t* status, int32_t* dk, int32_t* ck,
-                             int32_t* total_events, cudaStream_t s);
+// dk, ck [K] (zeroed here): events and censored subjects per group, n subjects;
+// *total_events (zeroed by the caller) += all events
+cudaError_t prep_group_stats(const int32_t* gend, int32_t K, const int8_t* status, int64_t n, int32_t* dk,
+                             int32_t* ck, int32_t* total_events, cudaStream_t s);
 cudaError_t prep_km(const int32_t* gend, const int32_t* ck, int32_t K, double* Gk, float2* Gkff, cudaStream_t s);
 cudaError_t prep_w2(const int32_t* gend, int32_t K, const int8_t* status, const double* Gk, void* w2, int prec,
                     cudaStream_t s);

@@ -404,7 +404,7 @@ int cox_nll_forward(const surv_nll_data* d, const float* B, double* nll, void* s
   NLL_TRY(ws_ensure(ws, W::GK, 4 * (size_t)K, &ck));
   NLL_TRY(cuda_err(prep_write_ends(time, n, static_cast<const int32_t*>(blk), static_cast<int32_t*>(gend), s),
                    "write ends"));
-  NLL_TRY(cuda_err(prep_group_stats(static_cast<int32_t*>(gend), K, status, static_cast<int32_t*>(dk),
+  NLL_TRY(cuda_err(prep_group_stats(static_cast<int32_t*>(gend), K, status, n, static_cast<int32_t*>(dk),
                                     static_cast<int32_t*>(ck), &ctrl->total_events, s),
                    "group stats"));
   // row partition of the scan kernels: two CTAs of 16 warps per SM

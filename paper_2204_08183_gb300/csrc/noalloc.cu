@@ -221,7 +221,7 @@ int run(const surv_data* d, int model, const double* beta, int32_t j, double* ou
   TAKE(rec, 8 * (size_t)K * M);
 
   TRY(survgpu::prep_write_ends(tp, n, static_cast<const int32_t*>(blockcnt), static_cast<int32_t*>(gend), s));
-  TRY(survgpu::prep_group_stats(static_cast<int32_t*>(gend), K, sp, static_cast<int32_t*>(dk),
+  TRY(survgpu::prep_group_stats(static_cast<int32_t*>(gend), K, sp, n, static_cast<int32_t*>(dk),
                                 static_cast<int32_t*>(ck), &ctrl->total_events, s));
   if (model == SURV_FG) {
     TRY(survgpu::prep_km(static_cast<int32_t*>(gend), static_cast<int32_t*>(ck), K, static_cast<double*>(Gk),

@@ -133,41 +133,45 @@ __global__ void k_write_ends(const int32_t* time, int64_t n, const int32_t* bloc
   if (f) gend[blockoff[blockIdx.x] + s_w[w] + __popc(m & ((1u << lane) - 1u))] = (int32_t)i;
 }
 
-// one warp per group: events (status 1) and censored (status 0) counts
-__global__ void k_group_stats(const int32_t* gend, int32_t K, const int8_t* status, int32_t* dk, int32_t* ck,
-                              int32_t* total_events) {
+// Events (status 1) and censored (status 0) per tie group.  Each warp takes
+// a chunk of kStatChunk consecutive subjects and adds the counts of every
+// group segment inside it to the group's total (integer atomics: the
+// result does not depend on their order).  A group spanning many chunks is
+// counted by many warps, so one large group does not hold up the kernel.
+constexpr int kStatChunk = 2048;
+__global__ void k_group_stats(const int32_t* gend, int32_t K, const int8_t* status, int64_t n, int32_t* dk,
+                              int32_t* ck, int32_t* total_events) {
   const int lane = threadIdx.x & 31;
   const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; k < K; k += nwarp) {
-  const int64_t a = k == 0 ? 0 : (int64_t)gend[k - 1] + 1, b = gend[k];
-  int d = 0, c = 0;
-  // eight independent loads in flight per lane
-  int64_t i = a + lane;
-  for (; i + 7 * 32 <= b; i += 8 * 32) {
-    int sv[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) sv[u] = status[i + 32 * u];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      d += sv[u] == 1;
-      c += sv[u] == 0;
+  const int64_t nchunk = (n + kStatChunk - 1) / kStatChunk;
+  for (int64_t ch = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; ch < nchunk; ch += nwarp) {
+    const int64_t r0 = ch * kStatChunk, r1 = min(r0 + kStatChunk, n);
+    // first group whose end is at or after r0
+    int lo = 0, hi = K - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if ((int64_t)gend[mid] >= r0) hi = mid; else lo = mid + 1;
     }
-  }
-  for (; i <= b; i += 32) {
-    const int s = status[i];
-    d += s == 1;
-    c += s == 0;
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    d += __shfl_down_sync(0xffffffffu, d, o);
-    c += __shfl_down_sync(0xffffffffu, c, o);
-  }
-  if (lane == 0) {
-    dk[k] = d;
-    if (ck) ck[k] = c;
-    if (d) atomicAdd(total_events, d);
-  }
+    int k = lo;
+    int evs = 0;
+    for (int64_t pos = r0; pos < r1 && k < K; ++k) {
+      const int64_t g_end = min((int64_t)gend[k], r1 - 1);
+      int d = 0, c = 0;
+      for (int64_t i = pos + lane; i <= g_end; i += 32) {
+        const int sv = status[i];
+        d += sv == 1;
+        c += sv == 0;
+      }
+      d = __reduce_add_sync(0xffffffffu, d);
+      c = __reduce_add_sync(0xffffffffu, c);
+      if (lane == 0) {
+        if (d) atomicAdd(dk + k, d);
+        if (ck && c) atomicAdd(ck + k, c);
+      }
+      evs += d;
+      pos = g_end + 1;
+    }
+    if (lane == 0 && evs) atomicAdd(total_events, evs);
   }
 }
 
@@ -430,11 +434,15 @@ cudaError_t prep_write_ends(const int32_t* time, int64_t n, const int32_t* block
   return cudaGetLastError();
 }
 
-cudaError_t prep_group_stats(const int32_t* gend, int32_t K, const int8_t* status, int32_t* dk, int32_t* ck,
-                             int32_t* total_events, cudaStream_t s) {
-  if (K <= 0) return cudaSuccess;
-  k_group_stats<<<grid_for((int64_t)K * 32, kPrepThreads, 16384), kPrepThreads, 0, s>>>(gend, K, status, dk, ck,
-                                                                                   total_events);
+cudaError_t prep_group_stats(const int32_t* gend, int32_t K, const int8_t* status, int64_t n, int32_t* dk,
+                             int32_t* ck, int32_t* total_events, cudaStream_t s) {
+  if (K <= 0 || n <= 0) return cudaSuccess;
+  cudaError_t st = cudaMemsetAsync(dk, 0, sizeof(int32_t) * (size_t)K, s);
+  if (st == cudaSuccess && ck) st = cudaMemsetAsync(ck, 0, sizeof(int32_t) * (size_t)K, s);
+  if (st != cudaSuccess) return st;
+  const int64_t nchunk = (n + kStatChunk - 1) / kStatChunk;
+  k_group_stats<<<grid_for(nchunk * 32, kPrepThreads, 16384), kPrepThreads, 0, s>>>(gend, K, status, n, dk, ck,
+                                                                                  total_events);
   return cudaGetLastError();
 }
 

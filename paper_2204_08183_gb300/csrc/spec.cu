@@ -487,7 +487,10 @@ cudaError_t capture_any_spec(const CcdParams& P, int B, int S, bool pdl, cudaStr
 }  // namespace
 
 // Slots (batches) per graph replay for p coordinates and B columns a batch.
-int spec_slots(int p, int B) { return std::max(8, (p + B - 1) / B + 2); }
+// About half a sweep's worth when most steps are zero: the replay in which
+// a fit stops, and the one queued behind it, run their remaining batches
+// empty, so shorter replays waste less.
+int spec_slots(int p, int B) { return std::max(8, ((p + B - 1) / B + 1) / 2 + 2); }
 
 cudaError_t run_spec_graph(const CcdParams& P, int B, cudaStream_t s, GraphCache* gc, cudaEvent_t t0, int* replays,
                            int* launches) {
@@ -504,7 +507,6 @@ cudaError_t run_spec_graph(const CcdParams& P, int B, cudaStream_t s, GraphCache
   if ((st = graph_cache_prepare(gc)) != cudaSuccess) return st;
   const char* env = std::getenv("SURVGPU_GRAPH_PDL");
   const bool pdl = !(env && env[0] == '0');
-  // batches per replay: about one sweep's worth when half the steps are zero
   const int S = spec_slots(P.p, B);
   const int mlp = 2000 + B * 2 + (pdl ? 1 : 0);
   if (!gc->exec || gc->mlp != mlp || std::memcmp(&gc->key, &P, sizeof(P)) != 0) {
