@@ -344,12 +344,17 @@ __global__ void __launch_bounds__(kStNT) k_strans(const __grid_constant__ CcdPar
   }
   __syncthreads();
   uint64_t* part = reinterpret_cast<uint64_t*>(P.slot_part);
+  // thread r sums partial r over the warps (fixed order) and stores it
+  if (tid < NP) {
+    ff a = s_red[0][tid];
+    for (int q = 1; q < kStWarps; ++q) a = ff_add(a, s_red[q][tid]);
+    part[(size_t)tid * G + c] = pack8(a);
+  }
+  __syncthreads();
   if (tid == 0) {
-    for (int r = 0; r < NP; ++r) {
-      ff a = s_red[0][r];
-      for (int q = 1; q < kStWarps; ++q) a = ff_add(a, s_red[q][r]);
-      part[(size_t)r * G + c] = pack8(a);
-    }
+    // the CTA's partials (stored by several threads, ordered before this
+    // thread by the barrier) are visible to whoever sees the count
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
     unsigned prev;
     asm volatile("atom.add.release.gpu.u32 %0, [%1], 1;" : "=r"(prev) : "l"(&ctl->ticket) : "memory");
     s_last = prev == (unsigned)(G - 1);
