@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(kStNT) k_strans(const __grid_constant__ CcdPar
     for (int qc = tid; qc < c; qc += kStNT)
 #pragma unroll
       for (int r = 0; r < R; ++r) t[r] = ff_add(t[r], unpack8<ff>(__ldcg(agg + (size_t)r * G + qc)));
-    warp_sum_some<R>(t);
+    warp_sum_n<R>(t);
     if (lane == 0)
 #pragma unroll
       for (int r = 0; r < R; ++r) s_wp[w][r] = t[r];
@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(kStNT) k_strans(const __grid_constant__ CcdPar
       v[B + b] = f2[b];
     }
     v[2 * B] = d_to_ff(pl);
-    warp_sum_some<NP>(v);
+    warp_sum_n<NP>(v);
     if (lane == 0)
 #pragma unroll
       for (int r = 0; r < NP; ++r) s_red[w][r] = v[r];
