@@ -263,7 +263,7 @@ def run_gpu(args, rank, world):
             # dram__bytes_read.sum + dram__bytes_write.sum of k_spass<4> +
             # k_strans<4> per row pass, steady state (ncu --cache-control
             # none); see profiles/k_spass_k_strans_cox_csc_n1e7.md
-            roofline["traffic"] = round((21353933 + 4378931) + (10547 + 38246))
+            roofline["traffic"] = round((21325107 + 4341018) + (13926 + 37350))
             roofline["traffic_note"] = "bytes per row pass, ncu steady-state capture of the kernels as committed"
         roofline["algorithmic_bytes_per_row_pass"] = round(alg_bytes / row_passes)
         roofline["us_per_row_pass"] = round(kern_ms * 1e3 / row_passes, 3)
