@@ -103,3 +103,18 @@ def test_product_path_does_not_import_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle", text, flags=re.M), f
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path, monkeypatch):
+    # no CPU fallback: a missing library is an error, not a silent substitute
+    monkeypatch.setattr(binding, "_lib", None)
+    with pytest.raises(RuntimeError, match="libsurvgpu.so not found"):
+        binding.load(str(tmp_path / "libsurvgpu.so"))
+
+
+def test_header_documents_every_flag_the_binding_uses():
+    text = open(HEADER).read()
+    for name in ("SURV_FLAG_TEST_STALL", "SURV_FLAG_PERSISTENT", "SURV_FLAG_CV_TUNE", "SURV_FLAG_SPARSE_NUMERATOR",
+                 "SURV_FLAG_ONE_COORDINATE"):
+        m = re.search(r"#define %s (\d+)" % name, text)
+        assert m and int(m.group(1)) == getattr(binding, name), name
