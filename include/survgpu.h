@@ -55,6 +55,9 @@ extern "C" {
 
 #define SURV_F32 0
 #define SURV_F64 1
+#define SURV_BF16 2      /* dense X only: bfloat16 values, widened on the device
+                            to the working precision (exactly: every bfloat16 is
+                            an FP32 value), so the fit is that of the rounded X */
 
 #define SURV_COX 0
 #define SURV_FG 1
@@ -76,9 +79,11 @@ extern "C" {
  *   layout = SURV_CSC:
  *     col_ptr [p+1] int64, col_ptr[0] = 0, non-decreasing; nnz = col_ptr[p].
  *     row_idx [nnz] int32, strictly increasing inside each column, in [0,n).
- *     values  [nnz] of dtype, or NULL for an all-ones (indicator) matrix.
+ *     values  [nnz] of dtype (SURV_F32 or SURV_F64), or NULL for an
+ *             all-ones (indicator) matrix.
  *   layout = SURV_DENSE:
- *     values  [n*p] of dtype, column-major (element (i,j) at j*n+i);
+ *     values  [n*p] of dtype (SURV_F32, SURV_F64 or SURV_BF16),
+ *             column-major (element (i,j) at j*n+i);
  *     col_ptr and row_idx are ignored.
  */
 typedef struct surv_data {

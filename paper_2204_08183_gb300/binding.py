@@ -32,7 +32,7 @@ SURV_E_NOMEM = -8
 SURV_E_INDEX = -9
 
 SURV_CSC, SURV_DENSE = 0, 1
-SURV_F32, SURV_F64 = 0, 1
+SURV_F32, SURV_F64, SURV_BF16 = 0, 1, 2
 SURV_COX, SURV_FG = 0, 1
 SURV_PEN = {"none": 0, "l1": 1, "l2": 2}
 SURV_PREC = {"f32c": 0, "f64": 1}
@@ -166,7 +166,9 @@ def _dtype_code(a):
         return SURV_F32
     if name.endswith("float64"):
         return SURV_F64
-    raise TypeError("values must be float32 or float64, got %s" % name)
+    if name.endswith("bfloat16"):
+        return SURV_BF16
+    raise TypeError("values must be float32, float64 or bfloat16 (dense X), got %s" % name)
 
 
 def _stream(stream):
@@ -188,8 +190,9 @@ class SurvData:
 
     Dense X: a column-major (n, p) array -- a Fortran-ordered numpy array, or
     a torch tensor holding X^T contiguously (shape (p, n)), passed with
-    ``layout="dense"``.  CSC: ``col_ptr`` (int64, p+1), ``row_idx`` (int32),
-    ``values`` (float32/float64 or None for indicators).  Arrays may live on
+    ``layout="dense"`` (float32, float64 or bfloat16).  CSC: ``col_ptr``
+    (int64, p+1), ``row_idx`` (int32), ``values`` (float32/float64 or None
+    for indicators).  Arrays may live on
     the host or on the GPU; references are kept alive by this object.
     """
 

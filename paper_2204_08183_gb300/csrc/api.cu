@@ -155,7 +155,10 @@ int check_data(const surv_data* d) {
   const int64_t n = d->n, p = d->p;
   if (n < 0 || p < 1 || n > 0x7fffffff || p > 0x7fffffff) { set_error("bad sizes n=%lld p=%lld", (long long)n, (long long)p); return SURV_E_INVALID; }
   if (d->layout != SURV_CSC && d->layout != SURV_DENSE) { set_error("bad layout"); return SURV_E_INVALID; }
-  if (d->dtype != SURV_F32 && d->dtype != SURV_F64) { set_error("bad dtype"); return SURV_E_INVALID; }
+  if (d->dtype != SURV_F32 && d->dtype != SURV_F64 && !(d->dtype == SURV_BF16 && d->layout == SURV_DENSE)) {
+    set_error("bad dtype (bfloat16 is for dense X only)");
+    return SURV_E_INVALID;
+  }
   if (n == 0) { set_error("no subjects"); return SURV_E_NO_EVENTS; }
   if (!d->time || !d->status) { set_error("null time/status"); return SURV_E_INVALID; }
   if (d->layout == SURV_CSC && (!d->col_ptr || !d->row_idx)) { set_error("null CSC arrays"); return SURV_E_INVALID; }
@@ -209,7 +212,7 @@ int stage_data(const surv_data* d, int prec, surv_workspace* ws, cudaStream_t s,
   }
   st->ld = n;
   if (d->layout == SURV_DENSE) {
-    const size_t vsz = d->dtype == SURV_F32 ? 4 : 8;
+    const size_t vsz = d->dtype == SURV_F32 ? 4 : (d->dtype == SURV_F64 ? 8 : 2);
     if ((rc = device_view(ws, W::VALUES, d->values, vsz * (size_t)n * (size_t)p, s, &vals_d))) return rc;
     const bool aligned = ((uintptr_t)vals_d % 16) == 0 && (n % 4) == 0;
     if (d->dtype != prec || !aligned) {
@@ -263,7 +266,10 @@ int fit_common(int model, const surv_data* d, const surv_opts* o_in, double* bet
   const int64_t n = d->n, p = d->p;
   if (n < 0 || p < 1 || n > 0x7fffffff || p > 0x7fffffff) { set_error("bad sizes n=%lld p=%lld", (long long)n, (long long)p); return SURV_E_INVALID; }
   if (d->layout != SURV_CSC && d->layout != SURV_DENSE) { set_error("bad layout"); return SURV_E_INVALID; }
-  if (d->dtype != SURV_F32 && d->dtype != SURV_F64) { set_error("bad dtype"); return SURV_E_INVALID; }
+  if (d->dtype != SURV_F32 && d->dtype != SURV_F64 && !(d->dtype == SURV_BF16 && d->layout == SURV_DENSE)) {
+    set_error("bad dtype (bfloat16 is for dense X only)");
+    return SURV_E_INVALID;
+  }
   if (o.penalty < 0 || o.penalty > 2 || o.precision < 0 || o.precision > 1) { set_error("bad penalty/precision"); return SURV_E_INVALID; }
   if (!(o.lambda >= 0.0) || !std::isfinite(o.lambda) || !(o.tol >= 0.0) || o.max_sweeps < 0) { set_error("bad lambda/tol/max_sweeps"); return SURV_E_INVALID; }
   if ((o.flags & ~(SURV_FLAG_TEST_STALL | SURV_FLAG_PERSISTENT | SURV_FLAG_SPARSE_NUMERATOR | SURV_FLAG_ONE_COORDINATE)) !=
@@ -607,7 +613,7 @@ int lambda_max_impl(const surv_data* d, const double* pf_in, double* out, void* 
   if ((rc = check_data(d))) return rc;
   const int64_t n = d->n, p = d->p;
   const int layout = d->layout;
-  const int prec = d->dtype == SURV_F32 ? 0 : 1;  // the data's own precision; the sums are FP64
+  const int prec = d->dtype == SURV_F64 ? 1 : 0;  // the data's own precision (bfloat16 widens to FP32); FP64 sums
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   surv_workspace ws;
   struct Free { surv_workspace* w; ~Free() { free_all(w); } } fr{&ws};

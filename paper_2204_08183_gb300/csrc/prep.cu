@@ -9,6 +9,7 @@
 // from the smallest time upward in a single thread, so its rounding follows
 // one fixed order.
 #include <climits>
+#include <cuda_bf16.h>
 #include <cmath>
 #include <type_traits>
 
@@ -369,12 +370,19 @@ __global__ void k_fill_f64(double* v, double value, int64_t count) {
     v[i] = value;
 }
 
+template <typename D, typename S>
+__device__ __forceinline__ D to_wide(S v) { return (D)v; }
+template <>
+__device__ __forceinline__ float to_wide<float, __nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <>
+__device__ __forceinline__ double to_wide<double, __nv_bfloat16>(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+
 template <typename S, typename D>
 __global__ void k_convert_dense(const S* src, int64_t n, int64_t p, D* dst, int64_t ld) {
   const int64_t total = ld * p;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t j = t / ld, i = t - j * ld;
-    dst[t] = i < n ? (D)src[j * n + i] : D(0);
+    dst[t] = i < n ? to_wide<D>(src[j * n + i]) : D(0);
   }
 }
 
@@ -542,6 +550,10 @@ cudaError_t prep_convert_dense(const void* src, int src_dtype, int64_t n, int64_
   const unsigned g = grid_for(ld * p, kPrepThreads, 16384);
   if (src_dtype == 0 && prec == 0) k_convert_dense<float, float><<<g, kPrepThreads, 0, s>>>((const float*)src, n, p, (float*)dst, ld);
   else if (src_dtype == 0) k_convert_dense<float, double><<<g, kPrepThreads, 0, s>>>((const float*)src, n, p, (double*)dst, ld);
+  else if (src_dtype == 2 && prec == 0)
+    k_convert_dense<__nv_bfloat16, float><<<g, kPrepThreads, 0, s>>>((const __nv_bfloat16*)src, n, p, (float*)dst, ld);
+  else if (src_dtype == 2)
+    k_convert_dense<__nv_bfloat16, double><<<g, kPrepThreads, 0, s>>>((const __nv_bfloat16*)src, n, p, (double*)dst, ld);
   else if (prec == 0) k_convert_dense<double, float><<<g, kPrepThreads, 0, s>>>((const double*)src, n, p, (float*)dst, ld);
   else k_convert_dense<double, double><<<g, kPrepThreads, 0, s>>>((const double*)src, n, p, (double*)dst, ld);
   return cudaGetLastError();

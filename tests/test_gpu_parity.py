@@ -286,3 +286,29 @@ def test_max_sweeps_reports_not_converged(lib, schedule):
     assert rc == binding.SURV_W_NOT_CONVERGED and info["sweeps"] == 0 and np.array_equal(beta, b0)
     ref = oracle.ccd_fit("cox", d["time"], d["status"], d["X"], "l2", 1.0, tol=0.0, max_sweeps=0, beta0=b0)
     assert abs(info["objective"] - ref["objective"]) <= 1e-6 * abs(ref["objective"])
+
+
+@pytest.mark.parametrize("prec", ["f32c", "f64"])
+def test_fit_dense_bfloat16_x(lib, prec):
+    # bfloat16 dense X is widened on the device: the fit is the oracle's fit
+    # of the rounded X
+    import torch
+    d = synth.cohort_cox_dense(6_000, 5, seed=51, n_true=3, beta_sd=0.5, grid=300)
+    Xb = torch.from_numpy(np.ascontiguousarray(d["X"].T.astype(np.float32))).to(torch.bfloat16)
+    sd = binding.SurvData(torch.from_numpy(d["time"]).cuda(), torch.from_numpy(d["status"]).cuda(), X=Xb.cuda())
+    assert sd.c.dtype == binding.SURV_BF16
+    beta, info, rc = binding.cox_fit(sd, penalty="l2", lam=1.0, tol=1e-10, precision=prec)
+    Xr = Xb.float().numpy().T.astype(np.float64)
+    ref = oracle.ccd_fit("cox", d["time"], d["status"], Xr, "l2", 1.0, tol=0.0, max_sweeps=info["sweeps"])
+    np.testing.assert_allclose(beta, ref["beta"], rtol=0, atol=1e-5 if prec == "f32c" else 1e-9)
+
+
+def test_bfloat16_csc_values_rejected(lib):
+    import torch
+    d = small_csc(500, 3, seed=52, density=0.3, n_times=40)
+    sd = binding.SurvData(torch.from_numpy(d["time"]).cuda(), torch.from_numpy(d["status"]).cuda(),
+                          col_ptr=torch.from_numpy(d["col_ptr"]).cuda(), row_idx=torch.from_numpy(d["row_idx"]).cuda(),
+                          values=torch.from_numpy(d["values"]).cuda().to(torch.bfloat16), n=500, p=3)
+    with pytest.raises(binding.SurvError) as e:
+        binding.cox_fit(sd, penalty="l2", lam=1.0)
+    assert e.value.code == binding.SURV_E_INVALID
