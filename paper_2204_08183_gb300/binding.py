@@ -189,8 +189,8 @@ class SurvData:
     """A cohort in the library's layout (subjects in decreasing time order).
 
     Dense X: a column-major (n, p) array -- a Fortran-ordered numpy array, or
-    a torch tensor holding X^T contiguously (shape (p, n)), passed with
-    ``layout="dense"`` (float32, float64 or bfloat16).  CSC: ``col_ptr``
+    a torch tensor holding X^T contiguously (shape (p, n)), passed as ``X``
+    (float32, float64 or bfloat16).  CSC: ``col_ptr``
     (int64, p+1), ``row_idx`` (int32), ``values`` (float32/float64 or None
     for indicators).  Arrays may live on
     the host or on the GPU; references are kept alive by this object.
