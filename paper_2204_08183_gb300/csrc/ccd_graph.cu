@@ -171,9 +171,12 @@ template <int MODEL, int LAYOUT, typename T, bool BATCH>
 __global__ void __launch_bounds__(kTransThreads) k_trans(const __grid_constant__ CcdParams P0, int j) {
   using A = typename AccOf<T>::type;
   constexpr int M = MODEL == 0 ? 3 : 6;
-  constexpr int NA = MODEL == 0 ? M : 2 * M;  // prefix sums (+ totals for Fine-Gray)
+  // prefix sums of the M components (+ for Fine-Gray the grand totals of
+  // the three suffix components 3..5, which the transform subtracts from)
+  constexpr int NA = MODEL == 0 ? M : M + 3;
   constexpr int NT = kTransThreads;
   __shared__ A s_wp[kTransWarps][NA];
+  __shared__ A s_tc[NA];
   __shared__ A s_base[kMaxWarpsPerCta][M];
   __shared__ A s_red[kTransWarps][3];
   __shared__ int s_last;
@@ -246,14 +249,14 @@ __global__ void __launch_bounds__(kTransThreads) k_trans(const __grid_constant__
       acc_zero(r[m]);
       if (tid < c) r[m] = x0;
       if (tid + NT < c) r[m] = acc_add(r[m], x1);
-      if (MODEL == 1) r[M + (m % M)] = acc_add(x0, x1);
+      if (MODEL == 1 && m >= 3) r[M + m - 3] = acc_add(x0, x1);
     }
     for (int qc = tid + 2 * NT; qc < G; qc += NT)  // grids above 512 CTAs
 #pragma unroll
       for (int m = 0; m < M; ++m) {
         const A x = unpack8<A>(__ldcg(agg + (size_t)m * G + qc));
         if (qc < c) r[m] = acc_add(r[m], x);
-        if (MODEL == 1) r[M + (m % M)] = acc_add(r[M + (m % M)], x);
+        if (MODEL == 1 && m >= 3) r[M + m - 3] = acc_add(r[M + m - 3], x);
       }
     warp_sum_n<NA>(r);
     if (lane == 0)
@@ -262,20 +265,22 @@ __global__ void __launch_bounds__(kTransThreads) k_trans(const __grid_constant__
   }
   __syncthreads();
   if (BATCH && s_stopped) return;  // this fit has stopped (the others go on)
-  // prefix before CTA c and (Fine-Gray) grand totals, same order everywhere
+  // prefix before CTA c and (Fine-Gray) grand totals: thread i sums value i
+  // over the warps in a fixed order, once for the CTA
+  if (tid < NA) {
+    A t = s_wp[0][tid];
+#pragma unroll 1
+    for (int qw = 1; qw < kTransWarps; ++qw) t = acc_add(t, s_wp[qw][tid]);
+    s_tc[tid] = t;
+  }
+  __syncthreads();
   A T_c[M], tot[M];
 #pragma unroll
   for (int m = 0; m < M; ++m) {
-    T_c[m] = s_wp[0][m];
-    if (MODEL == 1) tot[m] = s_wp[0][M + (m % M)];
+    T_c[m] = s_tc[m];
+    if (MODEL == 1 && m >= 3) tot[m] = s_tc[M + m - 3];
+    else acc_zero(tot[m]);
   }
-#pragma unroll 1
-  for (int qw = 1; qw < kTransWarps; ++qw)
-#pragma unroll
-    for (int m = 0; m < M; ++m) {
-      T_c[m] = acc_add(T_c[m], s_wp[qw][m]);
-      if (MODEL == 1) tot[m] = acc_add(tot[m], s_wp[qw][M + (m % M)]);
-    }
 
   // ---------------------------------------------- steps 3-4
   A fg1, fg2;
