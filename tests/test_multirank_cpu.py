@@ -120,6 +120,10 @@ def test_sharded_exchange_matches_single_rank():
         assert p.exitcode == 0
     for model, comp in [("cox", 0.0), ("fg", 0.25)]:
         dd = synth.cohort_small(4001, 3, seed=7, n_times=150, censor_frac=0.3, competing_frac=comp)
+        # the rank boundary falls inside a tie group (owned by rank 1, which
+        # holds its last subject): the case the exchange must get right
+        cut = np.linspace(0, 4001, world + 1).astype(int)[1]
+        assert dd["time"][cut - 1] == dd["time"][cut]
         for j in range(3):
             ref = oracle.model_terms(model, dd["time"], dd["status"], dd["X"], dd["beta"], j)
             for r in range(world):
