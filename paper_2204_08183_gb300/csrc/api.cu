@@ -1,7 +1,10 @@
 // C ABI of libsurvgpu.so (declared in include/survgpu.h): argument checks,
-// staging of host buffers, workspace management and the launch sequence
-// prep kernels -> persistent CCD kernel.  No arithmetic of the method runs
-// on the host; the host reads back only sizes, error words and results.
+// staging of host buffers, workspace management and the launch sequence:
+// prep kernels, then the CCD schedule (speculative coordinate batches for
+// Cox fits of CSC data in FP32, one coordinate per pass otherwise, both as
+// CUDA-graph replays; the persistent kernel on request and for single
+// evaluations).  No arithmetic of the method runs on the host; the host
+// reads back only sizes, error words and results.
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -352,7 +355,7 @@ int fit_common(int model, const surv_data* d, const surv_opts* o_in, double* bet
 
   // ---------------------------------------------------------- tables
   void *gend, *dk, *ck, *Gk, *rec, *e, *eta, *w2 = nullptr, *wk0, *woff = nullptr, *dTx, *beta, *width, *pen, *slots;
-  const size_t accsz = prec == 0 ? 8 : 8;  // ff (2 floats) or double
+  constexpr size_t accsz = 8;  // an accumulator: ff (2 floats) or double
   if ((rc = ensure(ws, W::GEND, 4 * (size_t)K, &gend))) return rc;
   if ((rc = ensure(ws, W::DK, 4 * (size_t)K, &dk))) return rc;
   if ((rc = ensure(ws, W::CK, 4 * (size_t)K, &ck))) return rc;
