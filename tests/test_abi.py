@@ -118,3 +118,32 @@ def test_header_documents_every_flag_the_binding_uses():
                  "SURV_FLAG_ONE_COORDINATE"):
         m = re.search(r"#define %s (\d+)" % name, text)
         assert m and int(m.group(1)) == getattr(binding, name), name
+
+
+def test_survdata_host_checks():
+    """Marshalling checks that run before any library call."""
+    import numpy as np
+    import torch
+    from paper_2204_08183_gb300 import binding
+    n, p = 64, 3
+    t = np.arange(n, 0, -1, dtype=np.int32)
+    s = np.ones(n, np.int8)
+    Xf = np.asfortranarray(np.ones((n, p), np.float32))
+    d = binding.SurvData(t, s, X=Xf)
+    assert (d.n, d.p, d.c.layout, d.c.dtype) == (n, p, binding.SURV_DENSE, binding.SURV_F32)
+    with pytest.raises(ValueError):
+        binding.SurvData(t, s, X=np.ascontiguousarray(Xf))          # C order is not column-major
+    with pytest.raises(ValueError):
+        binding.SurvData(t, s, X=torch.ones(n, p))                   # torch X must be (p, n)
+    d = binding.SurvData(t, s, X=torch.ones(p, n, dtype=torch.bfloat16))
+    assert d.c.dtype == binding.SURV_BF16 and d.p == p
+    with pytest.raises(TypeError):
+        binding.SurvData(t, s, X=np.asfortranarray(np.ones((n, p), np.int32)))
+    with pytest.raises(ValueError):
+        binding.SurvData(t, s, X=torch.ones(2 * p, n)[::2])          # not contiguous
+    cp = np.array([0, 2, 2, 4], np.int64)
+    ri = np.array([0, 5, 1, 7], np.int32)
+    d = binding.SurvData(t, s, col_ptr=cp, row_idx=ri)
+    assert (d.p, d.c.layout, d.c.dtype, d.c.values) == (3, binding.SURV_CSC, binding.SURV_F32, None)
+    d = binding.SurvData(t, s, col_ptr=cp, row_idx=ri, values=np.ones(4, np.float64))
+    assert d.c.dtype == binding.SURV_F64
