@@ -147,3 +147,58 @@ def test_survdata_host_checks():
     assert (d.p, d.c.layout, d.c.dtype, d.c.values) == (3, binding.SURV_CSC, binding.SURV_F32, None)
     d = binding.SurvData(t, s, col_ptr=cp, row_idx=ri, values=np.ones(4, np.float64))
     assert d.c.dtype == binding.SURV_F64
+
+
+def test_argument_errors_before_any_device_call(libpath):
+    """Argument checks of the fits, the evaluation, lambda_max and the CV
+    path return their codes before the first CUDA call, so they hold on a
+    host without a GPU too."""
+    import numpy as np
+    n = 50
+    t = np.arange(n, 0, -1, dtype=np.int32)
+    s = np.ones(n, np.int8)
+    cp = np.array([0, 3, 5], np.int64)
+    ri = np.array([1, 4, 9, 2, 3], np.int32)
+    good = binding.SurvData(t, s, col_ptr=cp, row_idx=ri)
+    beta = np.zeros(2)
+
+    def code(fn, *a, **kw):
+        with pytest.raises(binding.SurvError) as ei:
+            fn(*a, **kw)
+        return ei.value.code
+
+    E = binding
+    # sizes, layout, dtype
+    nop = binding.SurvData(t, s, col_ptr=np.zeros(1, np.int64), row_idx=ri)
+    assert code(binding.cox_fit, nop, beta=np.zeros(1)) == E.SURV_E_INVALID
+    bfc = binding.SurvData(t, s, col_ptr=cp, row_idx=ri, values=np.zeros(5, np.float32))
+    bfc.c.dtype = binding.SURV_BF16                       # bfloat16 is for dense X only
+    assert code(binding.cox_fit, bfc, beta=beta) == E.SURV_E_INVALID
+    bad_layout = binding.SurvData(t, s, col_ptr=cp, row_idx=ri)
+    bad_layout.c.layout = 7
+    assert code(binding.fg_fit, bad_layout, beta=beta) == E.SURV_E_INVALID
+    empty = binding.SurvData(t[:0], s[:0], col_ptr=np.zeros(3, np.int64), row_idx=ri[:0])
+    assert code(binding.cox_fit, empty, beta=beta) == E.SURV_E_NO_EVENTS
+    # options
+    assert code(binding.cox_fit, good, beta=beta, penalty="l1", lam=-1.0) == E.SURV_E_INVALID
+    assert code(binding.cox_fit, good, beta=beta, lam=float("nan")) == E.SURV_E_INVALID
+    assert code(binding.cox_fit, good, beta=beta, tol=-1.0) == E.SURV_E_INVALID
+    assert code(binding.cox_fit, good, beta=beta, max_sweeps=-1) == E.SURV_E_INVALID
+    assert code(binding.cox_fit, good, beta=beta, flags=1 << 20) == E.SURV_E_INVALID
+    # the sparse-numerator form is for Cox fits of CSC data in the FP32 mode
+    sn = binding.SURV_FLAG_SPARSE_NUMERATOR
+    assert code(binding.fg_fit, good, beta=beta, flags=sn) == E.SURV_E_INVALID
+    assert code(binding.cox_fit, good, beta=beta, flags=sn, precision="f64") == E.SURV_E_INVALID
+    assert code(binding.cox_fit, good, beta=beta, flags=sn | binding.SURV_FLAG_PERSISTENT) == E.SURV_E_INVALID
+    # single evaluation: coordinate out of range
+    assert code(binding.loglik_grad_hess, good, "cox", beta, 2) == E.SURV_E_INVALID
+    # CV path: fold and lambda counts, flags
+    fold = np.zeros(n, np.int8)
+    lam = np.ones(3)
+    assert code(binding.cox_cv_path, good, fold, 0, lam) == E.SURV_E_INVALID
+    assert code(binding.cox_cv_path, good, fold, 128, lam) == E.SURV_E_INVALID
+    assert code(binding.cox_cv_path, good, fold, 2, lam, ctas_per_fit=-1) == E.SURV_E_INVALID
+    assert code(binding.cox_cv_path, good, fold, 2, lam, flags=binding.SURV_FLAG_ONE_COORDINATE) == E.SURV_E_INVALID
+    assert code(binding.cox_cv_path, empty, fold, 2, lam) == E.SURV_E_NO_EVENTS
+    # lambda_max checks the data first
+    assert code(binding.cox_lambda_max, bad_layout) == E.SURV_E_INVALID
