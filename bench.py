@@ -254,6 +254,7 @@ def run_gpu(args, rank, world):
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)" if peaks else "fallback 6800 GB/s",
                 "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "frac_of_nominal_7900": round(achieved / 7900.0, 4),
                 "unit_of_work": "one coordinate (row pass + transform/Newton)",
                 "algorithmic_bytes_per_coordinate": round(alg_bytes / passes),
                 "us_per_coordinate": round(us_per_coord, 3),
@@ -744,6 +745,7 @@ def run_fg(args, rank, world):
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)" if peaks else "fallback 6800 GB/s",
                 "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "frac_of_nominal_7900": round(achieved / 7900.0, 4),
                 "unit_of_work": "one coordinate (row pass + transform/Newton)",
                 "algorithmic_bytes_per_coordinate": round(alg_bytes / passes),
                 "us_per_coordinate": round(kern_ms * 1e3 / passes, 3),
