@@ -675,9 +675,27 @@ __device__ __forceinline__ void warp_update(const CcdParams& P, int j, int gw, i
   } else {
     const T* xcol = reinterpret_cast<const T*>(P.X) + (size_t)j * P.ld;
     if constexpr (sizeof(T) == 4) {
-      for (int64_t i = r_lo + lane; i < r_hi; i += 32)
-        eta_axpy(reinterpret_cast<float2*>(P.eta), reinterpret_cast<float*>(P.e), i, (float)xcol[i], delta,
-                 P.fold_id && P.fold_id[i] == P.fold);
+      // loads batched 4 deep (x, then eta), then the stores: the element
+      // arithmetic is eta_axpy's, only more loads are in flight
+      float2* etap = reinterpret_cast<float2*>(P.eta);
+      float* ep = reinterpret_cast<float*>(P.e);
+      for (int64_t i0 = r_lo + lane; i0 < r_hi; i0 += 4 * 32) {
+        float xx[4];
+        float2 qq[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) xx[u] = i0 + 32 * u < r_hi ? (float)xcol[i0 + 32 * u] : 0.f;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) qq[u] = i0 + 32 * u < r_hi ? etap[i0 + 32 * u] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t i = i0 + 32 * u;
+          if (i >= r_hi) continue;
+          const ff v = ff_add({qq[u].x, qq[u].y}, ff_mul_f(delta, xx[u]));
+          etap[i] = make_float2(v.hi, v.lo);
+          const float ev = expf(v.hi);
+          ep[i] = (P.fold_id && P.fold_id[i] == P.fold) ? 0.f : fmaf(ev, v.lo, ev);
+        }
+      }
     } else {
       for (int64_t i = r_lo + lane; i < r_hi; i += 32)
         eta_axpy(reinterpret_cast<double*>(P.eta), reinterpret_cast<double*>(P.e), i, (double)xcol[i], applied,
