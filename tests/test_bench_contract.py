@@ -1,12 +1,15 @@
 """bench.py's output contract, checked on the CPU through its reference arm
 (the FP64 oracle on a small sample): one JSON line with the keys the
 benchmark contract names, the reference's own cpu_baseline and e2e, and
-nothing printed by ranks other than 0."""
+nothing printed by ranks other than 0; and the JSON assembly of the GPU
+arms with their device calls replaced by fakes."""
 import json
 import os
 import subprocess
 import sys
 import types
+
+import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -56,3 +59,69 @@ def test_workload_defaults():
         sys.argv = old
     assert a.gpus == 1 and a.warmup >= 3 and a.workload == "ccd" and a.impl == "gb300"
     assert a.n is None and a.p is None      # the workload's own size (1e7 x 100 for ccd)
+
+
+def test_gpu_arms_assemble_the_contract_line(monkeypatch):
+    """The JSON assembly of the GPU arms (headline Cox and Fine-Gray), run on
+    the host with the device calls replaced by fakes that return fixed fit
+    records: every key of the contract is present and derived as stated
+    (value = sweeps / device time, roofline fraction = achieved / peak).
+    No number here is a measurement."""
+    import torch
+    sys.path.insert(0, ROOT)
+    try:
+        import bench
+        import __graft_entry__
+        from paper_2204_08183_gb300 import binding
+    finally:
+        sys.path.remove(ROOT)
+
+    class Ev:
+        def __init__(self, enable_timing=True):
+            pass
+
+        def record(self, stream=None):
+            pass
+
+        def elapsed_time(self, other):
+            return 20.0                                       # ms for the timed fits
+
+    zeros = torch.zeros
+    monkeypatch.setattr(torch.cuda, "Event", Ev)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a, **k: None)
+    monkeypatch.setattr(torch.cuda, "set_device", lambda *a, **k: None)
+    monkeypatch.setattr(torch.cuda, "current_device", lambda: 0)
+    monkeypatch.setattr(torch.cuda, "current_stream", lambda *a, **k: None)
+    monkeypatch.setattr(torch.Tensor, "cuda", lambda self, *a, **k: self)
+    monkeypatch.setattr(torch.Tensor, "pin_memory", lambda self, *a, **k: self)
+    monkeypatch.setattr(torch, "zeros", lambda *a, **k: zeros(*a, **{x: v for x, v in k.items() if x != "device"}))
+    monkeypatch.setattr(__graft_entry__, "build", lambda: None)
+    monkeypatch.setattr(bench.time, "sleep", lambda s: None)
+
+    def fit(sd, beta=None, **kw):
+        return beta, {"sweeps": 4, "converged": 1, "loglik": -1.0, "n_groups": 100, "coordinate_passes": 40,
+                      "eta_updates": 30, "ccd_kernel_ms": 0.004, "kernel_launches": 90, "row_passes": 12,
+                      "nnz_beta": 3}, 0
+
+    monkeypatch.setattr(binding, "cox_fit", fit)
+    monkeypatch.setattr(binding, "fg_fit", fit)
+    monkeypatch.setattr(binding, "Workspace", lambda: None)
+    for argv, run in ((["--n", "20000", "--p", "10"], bench.run_gpu),
+                      (["--workload", "fg", "--n", "20000", "--p", "10"], bench.run_fg)):
+        monkeypatch.setattr(sys, "argv", ["bench.py"] + argv)
+        a = bench.parse()
+        out = run(a, 0, 1)
+        for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                  "scaling", "vs_baseline", "dtype", "data", "config", "roofline", "clocks", "gpu_launches",
+                  "e2e", "cpu_baseline"):
+            assert k in out, k
+        assert out["value"] == 4 * a.steps / 0.020
+        assert out["gpu_launches"] == 90 * a.steps
+        r = out["roofline"]
+        for k in ("bound", "achieved", "peak", "unit", "frac", "traffic"):
+            assert k in r, k
+        assert r["frac"] == pytest.approx(r["achieved"] / r["peak"], rel=1e-3, abs=1e-4) and r["frac"] > 0
+        e = out["e2e"]
+        assert e["unit"] == out["unit"] and e["h2d_bytes_per_step"] > 0 and e["d2h_bytes_per_step"] > 0
+        assert out["cpu_baseline"]["kind"] == "oracle" and out["cpu_baseline"]["cores"] >= 1
+        assert out["config"]["workload"].endswith("n20000_p10")
