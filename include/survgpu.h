@@ -156,6 +156,13 @@ typedef struct surv_opts {
  * take one coordinate per pass.)  This flag turns the batches off: one
  * coordinate per row pass, as the paper's schedule. */
 #define SURV_FLAG_ONE_COORDINATE 16
+/* Speculative batches of 8 coordinates per row pass instead of 4 (for
+ * comparison; 4 is the faster at the measured sizes). */
+#define SURV_FLAG_SPEC_B8 32
+/* Capture the per-coordinate and batch graphs without programmatic dependent
+ * launch (each kernel starts after the previous one has finished), for
+ * comparison with the default. */
+#define SURV_FLAG_NO_PDL 64
 
 /* Fill *opts with defaults: no penalty, FP32-compensated precision,
  * tol 1e-8, max_sweeps 1000, default stream, no workspace. */
@@ -254,15 +261,20 @@ int surv_groups(const int32_t *time, const int8_t *status, int64_t n, int64_t ma
  * that loads this library until the process exits.  A problem needs about
  * 12 bytes per subject (Cox, FP32; 16-24 for Fine-Gray or FP64), 52-76 bytes
  * per tie group and, for CSC, 19.5 KB per covariate; for example one million
- * subjects with 3650 distinct times and p = 100 fit.  A larger problem is
- * rejected with SURV_E_INVALID before any work is queued.  p <= 4096.
+ * subjects with 3650 distinct times and p = 100 fit.  A problem whose
+ * subject or covariate count needs more is rejected with SURV_E_INVALID
+ * before any work is queued; one whose tie groups need more is rejected
+ * after the validation and tie-group count kernels, which write only into
+ * the array.  p <= 4096.  col_ptr is copied to the host and checked
+ * (col_ptr[0] = 0, non-decreasing: SURV_E_INDEX otherwise) before any
+ * kernel reads row_idx through it.
  * The first call on a device looks up the array's device address and caches
  * it; make that first call before any stream capture.  All calls on a device
  * share the array, which keeps the last call's contents (the call zeroes
  * what must start at zero itself); calls that overlap on the GPU, from other
  * host threads or streams, race on it and must be serialised by the caller.
- *   data: time, status and X must be device arrays (there is no staging
- *   buffer); X values in the dtype that `precision` uses (SURV_PREC_F32C:
+ *   data: time, status and X must be arrays on the current device (or
+ *   managed memory; there is no staging buffer); X values in the dtype that `precision` uses (SURV_PREC_F32C:
  *   float32, SURV_PREC_F64: float64; CSC values may be NULL); dense X with a
  *   16-byte aligned base and n divisible by 4.  beta [p] host or device.
  *   loglik, grad, hess: host doubles (any may be NULL).  stream:

@@ -41,6 +41,8 @@ SURV_FLAG_PERSISTENT = 2
 SURV_FLAG_CV_TUNE = 4
 SURV_FLAG_SPARSE_NUMERATOR = 8
 SURV_FLAG_ONE_COORDINATE = 16
+SURV_FLAG_SPEC_B8 = 32
+SURV_FLAG_NO_PDL = 64
 
 # exported symbols, in the order the header declares them
 EXPORTS = ["surv_opts_default", "surv_workspace_create", "surv_workspace_destroy", "surv_sort_desc",
@@ -406,6 +408,29 @@ def cox_nll_backward(X, time, status, grad_nll, ncols, workspace, stream=None):
     return gB
 
 
+# Idle workspaces of the autograd function, per (device, stream): a forward
+# leases one and keeps it (eta and the risk-set sums live there) until its
+# autograd node is freed, which returns it for the next forward on the same
+# stream.  Reuse is ordered by the stream, and a training loop allocates
+# device memory only while the pool grows (once per graph alive at a time).
+_WS_POOL = {}
+
+
+class _WorkspaceLease:
+    def __init__(self, key):
+        idle = _WS_POOL.setdefault(key, [])
+        self.key = key
+        self.ws = idle.pop() if idle else Workspace()
+
+    def __del__(self):
+        ws, self.ws = getattr(self, "ws", None), None
+        if ws is not None:
+            try:
+                _WS_POOL.setdefault(self.key, []).append(ws)
+            except Exception:
+                pass
+
+
 def _cox_nll_function():
     import torch
 
@@ -413,20 +438,21 @@ def _cox_nll_function():
         """NLL_b(eta = X B) per column b as a differentiable function of B
         (X bfloat16 (n, p), time int32 and status int8 sorted by decreasing
         time, all on the GPU).  Forward and backward run in libsurvgpu; each
-        forward keeps its own workspace for its backward."""
+        forward holds a pooled workspace for its backward (see
+        _WorkspaceLease), so steady-state training steps allocate nothing."""
 
         @staticmethod
         def forward(ctx, B, X, time, status):
             B = B.contiguous()
-            ws = Workspace()
-            nll = cox_nll_forward(X, time, status, B, ws)
-            ctx.ws, ctx.X, ctx.time, ctx.status, ctx.ncols = ws, X, time, status, int(B.shape[1])
+            lease = _WorkspaceLease((B.device.index, torch.cuda.current_stream(B.device).cuda_stream))
+            nll = cox_nll_forward(X, time, status, B, lease.ws)
+            ctx.lease, ctx.X, ctx.time, ctx.status, ctx.ncols = lease, X, time, status, int(B.shape[1])
             return nll
 
         @staticmethod
         def backward(ctx, grad_out):
             g = grad_out.detach().to(torch.float64).contiguous()
-            gB = cox_nll_backward(ctx.X, ctx.time, ctx.status, g, ctx.ncols, ctx.ws)
+            gB = cox_nll_backward(ctx.X, ctx.time, ctx.status, g, ctx.ncols, ctx.lease.ws)
             return gB, None, None, None
 
     return CoxNLL

@@ -99,6 +99,8 @@ void free_all(surv_workspace* ws) {
   }
 }
 
+// Memory the kernels may read in place: device memory of the current device
+// or managed memory.  Host memory and memory of another GPU are not.
 bool is_device_ptr(const void* p) {
   if (!p) return false;
   cudaPointerAttributes a;
@@ -107,11 +109,19 @@ bool is_device_ptr(const void* p) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  if (a.type != cudaMemoryTypeDevice) return false;
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.device == cur;
 }
 
-// Device view of a caller array: the pointer itself if it is device memory,
-// else a workspace copy made on `s`.
+// Device view of a caller array: the pointer itself if the kernels may read
+// it in place, else a workspace copy made on `s` (from host memory or from
+// another GPU).
 int device_view(surv_workspace* ws, int id, const void* src, size_t bytes, cudaStream_t s, const void** out) {
   if (is_device_ptr(src) || bytes == 0) {
     *out = src;
@@ -120,7 +130,7 @@ int device_view(surv_workspace* ws, int id, const void* src, size_t bytes, cudaS
   void* d = nullptr;
   int rc = ensure(ws, id, bytes, &d);
   if (rc) return rc;
-  CUDA_TRY(cudaMemcpyAsync(d, src, bytes, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(d, src, bytes, cudaMemcpyDefault, s));
   *out = d;
   return SURV_OK;
 }
@@ -275,7 +285,8 @@ int fit_common(int model, const surv_data* d, const surv_opts* o_in, double* bet
   }
   if (o.penalty < 0 || o.penalty > 2 || o.precision < 0 || o.precision > 1) { set_error("bad penalty/precision"); return SURV_E_INVALID; }
   if (!(o.lambda >= 0.0) || !std::isfinite(o.lambda) || !(o.tol >= 0.0) || o.max_sweeps < 0) { set_error("bad lambda/tol/max_sweeps"); return SURV_E_INVALID; }
-  if ((o.flags & ~(SURV_FLAG_TEST_STALL | SURV_FLAG_PERSISTENT | SURV_FLAG_SPARSE_NUMERATOR | SURV_FLAG_ONE_COORDINATE)) !=
+  if ((o.flags & ~(SURV_FLAG_TEST_STALL | SURV_FLAG_PERSISTENT | SURV_FLAG_SPARSE_NUMERATOR | SURV_FLAG_ONE_COORDINATE |
+                   SURV_FLAG_SPEC_B8 | SURV_FLAG_NO_PDL)) !=
       0) {
     set_error("unknown flags");
     return SURV_E_INVALID;
@@ -364,15 +375,14 @@ int fit_common(int model, const surv_data* d, const surv_opts* o_in, double* bet
   if ((rc = ensure(ws, W::GKFF, 8 * (size_t)K, &Gkff))) return rc;
   // speculative coordinate batches (the default for Cox fits of CSC data in
   // the FP32 mode): 4 columns per row pass, the fastest measured at N = 10^7
-  // (8 columns: SURVGPU_SPEC_B=8, for comparison).  Not when the tie groups
+  // (8 columns: SURV_FLAG_SPEC_B8, for comparison).  Not when the tie groups
   // outnumber twice the warps: the transform of 4 columns at ~10^6 group
   // ends costs more than the passes saved (measured 107 against 68 ms per
   // fit at N = 2 x 10^6 with unique times).
   int spec_b = 0;
   if (!(o.flags & SURV_FLAG_ONE_COORDINATE) && graph && !sn && model == SURV_COX && layout == SURV_CSC &&
       prec == 0 && p >= 2 && (int64_t)K < 2 * (int64_t)nwarps) {
-    const char* eb = std::getenv("SURVGPU_SPEC_B");
-    spec_b = (eb && eb[0] == '8') ? 8 : 4;
+    spec_b = (o.flags & SURV_FLAG_SPEC_B8) ? 8 : 4;
   }
   const int R = spec_b ? 1 + 2 * spec_b : M;  // record / aggregate components
   if ((rc = ensure(ws, W::REC, accsz * (size_t)K * R, &rec))) return rc;
@@ -520,7 +530,7 @@ int fit_common(int model, const surv_data* d, const surv_opts* o_in, double* bet
   P.tol = o.tol;
   P.single_j = single_j;
   P.withhold_cta = (o.flags & SURV_FLAG_TEST_STALL) ? 0 : -1;
-  P.epoch0 = 0;
+  P.no_pdl = (o.flags & SURV_FLAG_NO_PDL) ? 1 : 0;
   P.timeout_ns = (uint64_t)((o.wait_limit_s > 0.0 ? o.wait_limit_s : 2.0) * 1e9);
   if (graph) {
     P.wt = static_cast<uint64_t*>(wt);
@@ -1041,7 +1051,7 @@ int surv_sort_desc(const int32_t* time, int64_t n, int32_t* perm, void* stream) 
   int launches = 0;
   CUDA_TRY(survgpu::radix_sort_desc(static_cast<const int32_t*>(tdev), n, static_cast<int32_t*>(pdev), work, s,
                                     &launches));
-  if (!perm_dev) CUDA_TRY(cudaMemcpyAsync(perm, pdev, 4 * (size_t)n, cudaMemcpyDeviceToHost, s));
+  if (!perm_dev) CUDA_TRY(cudaMemcpyAsync(perm, pdev, 4 * (size_t)n, cudaMemcpyDefault, s));
   CUDA_TRY(cudaStreamSynchronize(s));
   return SURV_OK;
 }

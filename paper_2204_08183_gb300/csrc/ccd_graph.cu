@@ -521,8 +521,7 @@ cudaError_t time_one_sweep(int model, int layout, int prec, const CcdParams& P, 
   } guard{&gc};
   cudaError_t st;
   if ((st = cudaStreamCreateWithFlags(&gc.cs, cudaStreamNonBlocking)) != cudaSuccess) return st;
-  const char* env = std::getenv("SURVGPU_GRAPH_PDL");
-  const bool pdl = !(env && env[0] == '0');
+  const bool pdl = !P.no_pdl;
   if ((st = capture_any(model, layout, prec, P, pdl, gc.cs, &guard.graph)) != cudaSuccess) return st;
   if ((st = cudaGraphInstantiate(&gc.exec, guard.graph, 0)) != cudaSuccess) return st;
   if ((st = cudaEventCreate(&guard.a)) != cudaSuccess) return st;
@@ -589,10 +588,9 @@ cudaError_t run_ccd_graph(int model, int layout, int prec, const CcdParams& P, c
   if (!gc) gc = &local;
   cudaError_t st;
   if ((st = graph_cache_prepare(gc)) != cudaSuccess) return st;
-  // programmatic dependent launch between the kernels; SURVGPU_GRAPH_PDL=0
+  // programmatic dependent launch between the kernels; SURV_FLAG_NO_PDL
   // turns it off (plain stream order), for comparison
-  const char* env = std::getenv("SURVGPU_GRAPH_PDL");
-  const bool pdl = !(env && env[0] == '0');
+  const bool pdl = !P.no_pdl;
   const int mlp = (model * 4 + layout * 2 + prec) * 2 + (pdl ? 1 : 0);
   if (!gc->exec || gc->mlp != mlp || std::memcmp(&gc->key, &P, sizeof(P)) != 0) {
     if (gc->exec) {

@@ -64,7 +64,7 @@ struct CcdParams {
   double tol;
   int32_t single_j;      // >= 0: evaluate coordinate single_j once and stop
   int32_t withhold_cta;  // test knob: this CTA never publishes (-1 = off)
-  unsigned epoch0;       // unused (counters restart at 0 every launch)
+  int32_t no_pdl;        // graph schedules: capture without programmatic dependent launch
   uint64_t timeout_ns;   // bound on every grid-exchange wait
 
   // per-coordinate kernel pair only (null for the persistent kernel)

@@ -318,6 +318,7 @@ int blas_err(cublasStatus_t e, const char* what) {
   return e == CUBLAS_STATUS_ALLOC_FAILED ? SURV_E_NOMEM : SURV_E_CUDA;
 }
 
+// Device memory of the current device, or managed memory.
 bool on_device(const void* p) {
   if (!p) return false;
   cudaPointerAttributes a;
@@ -325,7 +326,13 @@ bool on_device(const void* p) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice && a.device == cur;
 }
 
 int get_blas(surv_workspace* ws, cudaStream_t s, cublasHandle_t* h) {

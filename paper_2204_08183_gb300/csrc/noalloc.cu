@@ -83,24 +83,24 @@ struct Carve {
   }
 };
 
-bool on_device(const void* p) {
+// Device memory of the current device (or managed memory, which any device
+// may read).  Memory of another GPU is refused: the kernels run here.
+bool on_device(const void* p, int dev) {
   if (!p) return false;
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
-__global__ void k_check_colptr(const int64_t* col_ptr, int64_t p, unsigned* perr) {
-  unsigned bits = 0;
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < p; j += (int64_t)gridDim.x * blockDim.x) {
-    if (col_ptr[j + 1] < col_ptr[j]) bits |= survgpu::PREP_INDEX;
-    if (j == 0 && col_ptr[0] != 0) bits |= survgpu::PREP_INDEX;
-  }
-  if (bits) atomicOr(perr, bits);
-}
+// Host copies of beta and col_ptr (each at most kMaxP + 1 entries) for the
+// calling thread: the column bounds are checked here before any kernel reads
+// through them.
+thread_local double g_beta_h[kMaxP];
+thread_local int64_t g_colptr_h[kMaxP + 1];
 
 int map_prep(unsigned perr) {
   if (perr & survgpu::PREP_INDEX) { snprintf(g_err, sizeof(g_err), "malformed CSC indices"); return SURV_E_INDEX; }
@@ -147,13 +147,16 @@ int run(const surv_data* d, int model, const double* beta, int32_t j, double* ou
     return SURV_E_INVALID;
   }
   const bool csc = d->layout == SURV_CSC;
-  if (!on_device(d->time) || !on_device(d->status) || (csc && (!on_device(d->col_ptr) || !on_device(d->row_idx))) ||
-      ((!csc || d->values) && !on_device(d->values))) {
-    snprintf(g_err, sizeof(g_err), "time, status and X must be device arrays");
-    return SURV_E_INVALID;
-  }
   if (!csc && ((uintptr_t)d->values % 16 != 0 || n % 4 != 0)) {
     snprintf(g_err, sizeof(g_err), "dense X needs a 16-byte aligned base and n divisible by 4");
+    return SURV_E_INVALID;
+  }
+  int cur = 0;
+  TRY(cudaGetDevice(&cur));
+  if (!on_device(d->time, cur) || !on_device(d->status, cur) ||
+      (csc && (!on_device(d->col_ptr, cur) || !on_device(d->row_idx, cur))) ||
+      ((!csc || d->values) && !on_device(d->values, cur))) {
+    snprintf(g_err, sizeof(g_err), "time, status and X must be arrays on the current device");
     return SURV_E_INVALID;
   }
 
@@ -171,9 +174,24 @@ int run(const surv_data* d, int model, const double* beta, int32_t j, double* ou
   const size_t tsz = prec == SURV_PREC_F32C ? 4 : 8;
   const int M = model == SURV_COX ? 3 : 6;
 
-  // host copies of beta (the caller's beta may be host or device memory)
-  double beta_h[kMaxP];
+  // host copies of beta (the caller's beta may be host or device memory) and
+  // of col_ptr, checked before any kernel indexes row_idx through it
+  double* beta_h = g_beta_h;
+  int64_t* colptr_h = g_colptr_h;
   TRY(cudaMemcpyAsync(beta_h, beta, 8 * (size_t)p, cudaMemcpyDefault, s));
+  if (csc) TRY(cudaMemcpyAsync(colptr_h, d->col_ptr, 8 * (size_t)(p + 1), cudaMemcpyDeviceToHost, s));
+  TRY(cudaStreamSynchronize(s));
+  if (csc) {
+    if (colptr_h[0] != 0) { snprintf(g_err, sizeof(g_err), "col_ptr[0] != 0"); return SURV_E_INDEX; }
+    for (int64_t q = 0; q < p; ++q)
+      if (colptr_h[q + 1] < colptr_h[q]) {
+        snprintf(g_err, sizeof(g_err), "col_ptr decreases at %lld", (long long)q);
+        return SURV_E_INDEX;
+      }
+    if (colptr_h[p] > 0x7fffffffLL) { snprintf(g_err, sizeof(g_err), "more than 2^31 - 1 nonzeros"); return SURV_E_INDEX; }
+  }
+  for (int64_t q = 0; q < p; ++q)
+    if (!std::isfinite(beta_h[q])) { snprintf(g_err, sizeof(g_err), "non-finite beta"); return SURV_E_NONFINITE; }
 
   void *ctrl_v, *blockcnt, *e, *eta, *w2 = nullptr, *wk0, *woff = nullptr, *dTx, *beta_d, *width, *pen, *slots;
   TAKE(ctrl_v, sizeof(Ctrl));
@@ -197,8 +215,6 @@ int run(const surv_data* d, int model, const double* beta, int32_t j, double* ou
   const int8_t* sp = d->status;
   TRY(survgpu::prep_check_times(tp, sp, n, model, &ctrl->perr, s));
   if (csc) {
-    k_check_colptr<<<(unsigned)((p + 255) / 256), 256, 0, s>>>(d->col_ptr, p, &ctrl->perr);
-    TRY(cudaGetLastError());
     TRY(survgpu::prep_check_csc(d->col_ptr, d->row_idx, d->values, prec, p, n, &ctrl->perr, s));
   } else {
     TRY(survgpu::prep_check_dense(d->values, prec, n, n, p, &ctrl->perr, s));
@@ -208,8 +224,6 @@ int run(const surv_data* d, int model, const double* beta, int32_t j, double* ou
   TRY(cudaMemcpyAsync(&hc, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
   TRY(cudaStreamSynchronize(s));
   if ((rc = map_prep(hc.perr))) return rc;
-  for (int64_t q = 0; q < p; ++q)
-    if (!std::isfinite(beta_h[q])) { snprintf(g_err, sizeof(g_err), "non-finite beta"); return SURV_E_NONFINITE; }
   const int32_t K = hc.K;
 
   void *gend, *dk, *ck, *Gk, *Gkff, *rec;
@@ -245,14 +259,11 @@ int run(const surv_data* d, int model, const double* beta, int32_t j, double* ou
   } else if (!csc) {
     TRY(survgpu::prep_eta_dense(d->values, prec, n, n, p, static_cast<double*>(beta_d), eta, e, s));
   } else {
-    int64_t colptr_h[2];
     TRY(survgpu::prep_eta_zero(prec, n, eta, e, s));
     for (int64_t q = 0; q < p; ++q) {
       if (beta_h[q] == 0.0) continue;
-      TRY(cudaMemcpyAsync(colptr_h, d->col_ptr + q, 16, cudaMemcpyDeviceToHost, s));
-      TRY(cudaStreamSynchronize(s));
-      const void* vq = d->values ? static_cast<const char*>(d->values) + tsz * (size_t)colptr_h[0] : nullptr;
-      TRY(survgpu::prep_eta_axpy_csc(nullptr, d->row_idx + colptr_h[0], vq, prec, q, colptr_h[1] - colptr_h[0],
+      const void* vq = d->values ? static_cast<const char*>(d->values) + tsz * (size_t)colptr_h[q] : nullptr;
+      TRY(survgpu::prep_eta_axpy_csc(nullptr, d->row_idx + colptr_h[q], vq, prec, q, colptr_h[q + 1] - colptr_h[q],
                                      beta_h[q], eta, s));
     }
     TRY(survgpu::prep_eta_exp(prec, n, eta, e, s));

@@ -176,19 +176,77 @@ __global__ void k_group_stats(const int32_t* gend, int32_t K, const int8_t* stat
   }
 }
 
-// G(t_k) = prod_{k' >= k} (1 - c_k' / n_k'), n_k' = e_k' + 1 (Section 2.2,
-// Kaplan-Meier of the censoring times; groups k' >= k have t_k' <= t_k).
-__global__ void k_km(const int32_t* gend, const int32_t* ck, int32_t K, double* Gk, float2* Gkff) {
-  if (blockIdx.x != 0 || threadIdx.x != 0) return;
-  double acc = 1.0;
-  for (int64_t k = (int64_t)K - 1; k >= 0; --k) {
-    const double f = 1.0 - (double)ck[k] / (double)((int64_t)gend[k] + 1);
-    acc = acc * f;
-    Gk[k] = acc;
-    if (Gkff) {
-      const ff v = d_to_ff(acc);
-      Gkff[k] = make_float2(v.hi, v.lo);
+// Kaplan-Meier censoring survival (Section 2.2):
+//   G(t_k) = prod_{k' >= k} f_k',  f_k' = 1 - c_k' / n_k',  n_k' = e_k' + 1
+// (groups k' >= k have t_k' <= t_k).  The factors are independent: one
+// thread each (k_km_factor writes them into Gk).  The product is ordered:
+// up to kKmSerial groups one thread multiplies them in the order of the
+// definition, k = K - 1 down to 0, exactly as a sequential loop does; above
+// that the groups are cut into 1024 contiguous chunks, each thread forms
+// its chunk's product, a fixed-shape suffix scan over the chunks gives each
+// chunk the product of the chunks after it, and each thread walks its chunk
+// downward from there.  That order is fixed (the result does not depend on
+// timing) and keeps the relative error below (2 L + 12) u, L = ceil(K /
+// 1024), against (K - 1) u for the sequential product.
+constexpr int kKmSerial = 4096;
+constexpr int kKmThreads = 1024;
+
+__global__ void k_km_factor(const int32_t* gend, const int32_t* ck, int32_t K, double* f) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K; k += (int64_t)gridDim.x * blockDim.x)
+    f[k] = 1.0 - (double)ck[k] / (double)((int64_t)gend[k] + 1);
+}
+
+__device__ __forceinline__ void km_put(double* Gk, float2* Gkff, int64_t k, double v) {
+  Gk[k] = v;
+  if (Gkff) {
+    const ff q = d_to_ff(v);
+    Gkff[k] = make_float2(q.hi, q.lo);
+  }
+}
+
+// Gk holds the factors on entry and G(t_k) on exit (one block).
+__global__ void __launch_bounds__(kKmThreads) k_km_product(int32_t K, double* Gk, float2* Gkff) {
+  if (K <= kKmSerial) {
+    if (threadIdx.x != 0) return;
+    double acc = 1.0;
+    for (int64_t k = (int64_t)K - 1; k >= 0; --k) {
+      acc = acc * Gk[k];
+      km_put(Gk, Gkff, k, acc);
     }
+    return;
+  }
+  __shared__ double s_w[32];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int64_t L = ((int64_t)K + kKmThreads - 1) / kKmThreads;
+  const int64_t a = min((int64_t)t * L, (int64_t)K), b = min(a + L, (int64_t)K);
+  double v = 1.0;
+  for (int64_t k = b - 1; k >= a; --k) v = v * Gk[k];
+  // inclusive suffix products over the lanes, then over the warps
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const double u = __shfl_down_sync(0xffffffffu, v, d);
+    if (lane + d < 32) v = v * u;
+  }
+  if (lane == 0) s_w[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    double q = s_w[lane];
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const double u = __shfl_down_sync(0xffffffffu, q, d);
+      if (lane + d < 32) q = q * u;
+    }
+    __syncwarp();
+    s_w[lane] = q;
+  }
+  __syncthreads();
+  double in_warp = __shfl_down_sync(0xffffffffu, v, 1);
+  if (lane == 31) in_warp = 1.0;
+  const double later_warps = w < 31 ? s_w[w + 1] : 1.0;
+  double acc = later_warps * in_warp;   // product of the chunks after this one
+  for (int64_t k = b - 1; k >= a; --k) {
+    acc = acc * Gk[k];
+    km_put(Gk, Gkff, k, acc);
   }
 }
 
@@ -455,7 +513,11 @@ cudaError_t prep_group_stats(const int32_t* gend, int32_t K, const int8_t* statu
 }
 
 cudaError_t prep_km(const int32_t* gend, const int32_t* ck, int32_t K, double* Gk, float2* Gkff, cudaStream_t s) {
-  k_km<<<1, 32, 0, s>>>(gend, ck, K, Gk, Gkff);
+  if (K <= 0) return cudaSuccess;
+  k_km_factor<<<grid_for(K, kPrepThreads, 16384), kPrepThreads, 0, s>>>(gend, ck, K, Gk);
+  cudaError_t st = cudaGetLastError();
+  if (st != cudaSuccess) return st;
+  k_km_product<<<1, kKmThreads, 0, s>>>(K, Gk, Gkff);
   return cudaGetLastError();
 }
 

@@ -532,8 +532,7 @@ cudaError_t run_sn_graph(const CcdParams& P, const SnParams& S, cudaStream_t s, 
   if (!gc) gc = &local;
   cudaError_t st;
   if ((st = graph_cache_prepare(gc)) != cudaSuccess) return st;
-  const char* env = std::getenv("SURVGPU_GRAPH_PDL");
-  const bool pdl = !(env && env[0] == '0');
+  const bool pdl = !P.no_pdl;
   const int mlp = 1000 + (pdl ? 1 : 0);
   unsigned char key2[sizeof(GraphCache::key2)] = {};
   std::memcpy(key2, &S, sizeof(S));

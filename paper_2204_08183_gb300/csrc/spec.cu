@@ -510,8 +510,7 @@ cudaError_t run_spec_graph(const CcdParams& P, int B, cudaStream_t s, GraphCache
   if (!gc) gc = &local;
   cudaError_t st;
   if ((st = graph_cache_prepare(gc)) != cudaSuccess) return st;
-  const char* env = std::getenv("SURVGPU_GRAPH_PDL");
-  const bool pdl = !(env && env[0] == '0');
+  const bool pdl = !P.no_pdl;
   const int S = spec_slots(P.p, B);
   const int mlp = 2000 + B * 2 + (pdl ? 1 : 0);
   if (!gc->exec || gc->mlp != mlp || std::memcmp(&gc->key, &P, sizeof(P)) != 0) {

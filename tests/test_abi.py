@@ -96,6 +96,13 @@ int main(void) {
         assert getattr(structs[sname], field).offset == int(off), key
 
 
+def test_library_reads_no_environment_knobs():
+    # every schedule choice goes through surv_opts.flags
+    csrc = os.path.join(ROOT, "paper_2204_08183_gb300", "csrc")
+    for f in os.listdir(csrc):
+        assert "getenv" not in open(os.path.join(csrc, f)).read(), f
+
+
 def test_product_path_does_not_import_oracle():
     pkg = os.path.join(ROOT, "paper_2204_08183_gb300")
     for dirpath, _, files in os.walk(pkg):
@@ -115,7 +122,7 @@ def test_binding_fails_loudly_without_the_library(tmp_path, monkeypatch):
 def test_header_documents_every_flag_the_binding_uses():
     text = open(HEADER).read()
     for name in ("SURV_FLAG_TEST_STALL", "SURV_FLAG_PERSISTENT", "SURV_FLAG_CV_TUNE", "SURV_FLAG_SPARSE_NUMERATOR",
-                 "SURV_FLAG_ONE_COORDINATE"):
+                 "SURV_FLAG_ONE_COORDINATE", "SURV_FLAG_SPEC_B8", "SURV_FLAG_NO_PDL"):
         m = re.search(r"#define %s (\d+)" % name, text)
         assert m and int(m.group(1)) == getattr(binding, name), name
 
@@ -202,3 +209,40 @@ def test_argument_errors_before_any_device_call(libpath):
     assert code(binding.cox_cv_path, empty, fold, 2, lam) == E.SURV_E_NO_EVENTS
     # lambda_max checks the data first
     assert code(binding.cox_lambda_max, bad_layout) == E.SURV_E_INVALID
+
+
+def test_noalloc_argument_errors_before_any_device_call(libpath):
+    """loglik_grad_hess_noalloc rejects out-of-range sizes, a bad coordinate,
+    values whose dtype differs from the precision and misaligned dense X
+    before its first CUDA call."""
+    import numpy as np
+    n = 40
+    t = np.arange(n, 0, -1, dtype=np.int32)
+    s = np.ones(n, np.int8)
+
+    def code(*a, **kw):
+        with pytest.raises(binding.SurvError) as ei:
+            binding.loglik_grad_hess_noalloc(*a, **kw)
+        return ei.value.code
+
+    E = binding
+    wide = 4097                                              # more covariates than the limit
+    cpw = np.zeros(wide + 1, np.int64)
+    dw = binding.SurvData(t, s, col_ptr=cpw, row_idx=np.zeros(1, np.int32), p=wide)
+    assert code(dw, "cox", np.zeros(wide), 0) == E.SURV_E_INVALID
+    cp = np.array([0, 3, 5], np.int64)
+    ri = np.array([1, 4, 9, 2, 3], np.int32)
+    good = binding.SurvData(t, s, col_ptr=cp, row_idx=ri)
+    assert code(good, "cox", np.zeros(2), 2) == E.SURV_E_INVALID           # j out of range
+    assert code(good, "cox", np.zeros(2), -1) == E.SURV_E_INVALID
+    f64 = binding.SurvData(t, s, col_ptr=cp, row_idx=ri, values=np.ones(5, np.float64))
+    assert code(f64, "cox", np.zeros(2), 0) == E.SURV_E_INVALID             # float64 values, FP32 mode
+    X = np.asfortranarray(np.ones((n, 2), np.float32))
+    assert code(binding.SurvData(t, s, X=X), "cox", np.zeros(2), 0, precision="f64") == E.SURV_E_INVALID
+    n3 = 39                                                  # dense X needs n divisible by 4
+    d3 = binding.SurvData(t[:n3], s[:n3], X=np.asfortranarray(np.ones((n3, 2), np.float32)))
+    assert code(d3, "cox", np.zeros(2), 0) == E.SURV_E_INVALID
+    buf = np.zeros(2 * n + 4, np.float32)
+    mis = buf[1:1 + 2 * n].reshape(2, n).T                   # 4-byte offset base: not 16-byte aligned
+    assert mis.flags["F_CONTIGUOUS"] and mis.ctypes.data % 16 != 0
+    assert code(binding.SurvData(t, s, X=mis), "cox", np.zeros(2), 0) == E.SURV_E_INVALID

@@ -1,8 +1,10 @@
 """GPU parity: the CUDA path through the C ABI against the FP64 oracle.
 
 Integer work (sort permutation, tie-group ends, event counts) must match
-bit for bit; the Kaplan-Meier product runs in the same order in FP64 and
-must match bit for bit too.  Floating results follow the tolerances derived
+bit for bit.  The Kaplan-Meier product runs in the order of its definition
+for up to 4096 tie groups and must then match bit for bit too; beyond that
+it runs as a fixed-order chunked product and is held to the error bound of
+an FP64 product of K factors.  Floating results follow the tolerances derived
 in the design notes: the FP32-compensated mode stores e = exp(eta) in FP32
 (relative error ~1e-7 per term) and accumulates in float-float, so
 l is within 1e-6 relative and l', l'' within 1e-6 of the scale
@@ -62,6 +64,47 @@ def test_groups_bit_exact(lib, n, n_times):
     assert np.array_equal(gend, og.astype(np.int32))
     assert np.array_equal(dk, oracle.group_counts(og, st, 1).astype(np.int32))
     assert np.array_equal(Gk, oracle.km_censoring_groups(t, st, og))   # same order of FP64 products
+
+
+@pytest.mark.parametrize("K", [4096, 4097, 2_000_003])
+def test_groups_many_km_factors(lib, K):
+    """K tie groups with censoring in most of them: up to 4096 the product is
+    sequential (bit-exact); above, a chunked product whose relative error,
+    like the sequential one's, stays below K u (u = 2^-53) of the exact
+    value, so the two differ by at most 2 K u relative."""
+    rng = np.random.default_rng(K)
+    n = K + K // 3
+    t = np.sort(rng.choice(np.arange(1, 4 * K + 1), size=K, replace=False))[::-1].astype(np.int32)
+    t = np.sort(np.concatenate([t, rng.choice(t, size=n - K)]))[::-1].astype(np.int32)
+    st = rng.choice(np.array([0, 1, 2], np.int8), size=n, p=[0.5, 0.3, 0.2])
+    gend, dk, Gk = binding.surv_groups(t, st)
+    og = oracle.tie_groups(t)
+    assert og.shape[0] == K
+    assert np.array_equal(gend, og.astype(np.int32))
+    assert np.array_equal(dk, oracle.group_counts(og, st, 1).astype(np.int32))
+    ref = oracle.km_censoring_groups(t, st, og)
+    assert ref.min() < 1e-3                          # a long product, far from 1
+    if K <= 4096:
+        assert np.array_equal(Gk, ref)
+    else:
+        np.testing.assert_allclose(Gk, ref, rtol=2 * K * 2.0 ** -53, atol=0)
+
+
+def test_fg_fit_near_unique_times(lib):
+    """Fine-Gray fit where almost every subject has its own time (K close to
+    N): the censoring weights come from the chunked Kaplan-Meier product and
+    every warp of the row pass holds many group ends."""
+    n, p = 200_003, 4
+    d = synth.cohort_small(n, p, seed=31, n_times=50 * n, censor_frac=0.3, competing_frac=0.25)
+    st = d["status"]
+    K = oracle.tie_groups(d["time"]).shape[0]
+    assert K > 0.9 * n
+    sd = survdata(d)
+    beta, info, rc = binding.fg_fit(sd, penalty="l2", lam=2.0, tol=0.0, max_sweeps=3)
+    ref = oracle.ccd_fit("fg", d["time"], st, d["X"], "l2", 2.0, tol=0.0, max_sweeps=3)
+    assert info["sweeps"] == 3 and info["n_groups"] == K
+    np.testing.assert_allclose(beta, ref["beta"], rtol=0, atol=1e-5)
+    assert info["loglik"] == pytest.approx(ref["loglik"], rel=1e-6)
 
 
 # ------------------------------------------------------------ one pass

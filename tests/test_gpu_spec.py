@@ -19,10 +19,10 @@ SPEC = 0                                   # the default
 ONE = binding.SURV_FLAG_ONE_COORDINATE
 
 
-@pytest.fixture(params=["4", "8"])
-def batch(request, monkeypatch):
-    monkeypatch.setenv("SURVGPU_SPEC_B", request.param)
-    return int(request.param)
+@pytest.fixture(params=[0, binding.SURV_FLAG_SPEC_B8], ids=["B4", "B8"])
+def batch(request):
+    """Extra flags selecting 4 (default) or 8 coordinates per batch."""
+    return request.param
 
 
 @pytest.mark.parametrize("binary", [True, False])
@@ -32,7 +32,7 @@ def test_spec_fit_matches_oracle_l1(lib, batch, binary, n, p, n_times):
     lmax = oracle.lambda_max("cox", d["time"], d["status"], oracle_X(d))
     lam = 0.3 * lmax
     sd = survdata(d)
-    beta, info, rc = binding.cox_fit(sd, penalty="l1", lam=lam, tol=1e-7, max_sweeps=200, flags=SPEC)
+    beta, info, rc = binding.cox_fit(sd, penalty="l1", lam=lam, tol=1e-7, max_sweeps=200, flags=SPEC | batch)
     ref = oracle.ccd_fit("cox", d["time"], d["status"], oracle_X(d), "l1", lam, tol=0.0,
                          max_sweeps=info["sweeps"])
     np.testing.assert_allclose(beta, ref["beta"], rtol=0, atol=1e-5)
@@ -47,7 +47,7 @@ def test_spec_l2_all_nonzero_steps(lib, batch):
     # L2 with small lambda: nearly every step is nonzero (batches of one)
     d = small_csc(5000, 9, seed=5, density=0.3, n_times=500)
     sd = survdata(d)
-    b1, i1, _ = binding.cox_fit(sd, penalty="l2", lam=0.5, tol=1e-7, flags=SPEC)
+    b1, i1, _ = binding.cox_fit(sd, penalty="l2", lam=0.5, tol=1e-7, flags=SPEC | batch)
     ref = oracle.ccd_fit("cox", d["time"], d["status"], oracle_X(d), "l2", 0.5, tol=0.0, max_sweeps=i1["sweeps"])
     np.testing.assert_allclose(b1, ref["beta"], rtol=0, atol=1e-5)
 
@@ -64,7 +64,9 @@ def test_spec_max_sweeps_zero_and_one(lib):
 
 
 def test_spec_headline_size(lib):
-    """N = 10^7, p = 100 binary at 5 %, L1 lambda = 1e-4 N."""
+    """N = 10^7, p = 100 binary at 5 %, L1 lambda = 1e-4 N: the batched and
+    the one-coordinate schedules agree (a check of the schedule, GPU against
+    GPU; the oracle parity of this fit is tests/test_gpu_fullsize.py)."""
     d = synth.cohort_cox_sparse(10_000_000, 100, seed=2, density=0.05, n_true=10, laplace_scale=0.2,
                                 censor_frac=0.5, grid=3650)
     sd = survdata(d)

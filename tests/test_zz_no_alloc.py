@@ -59,3 +59,22 @@ def test_noalloc_rejects_oversize_and_host_arrays(lib):
     with pytest.raises(binding.SurvError) as ei:
         binding.loglik_grad_hess_noalloc(survdata(small, "host"), "cox", np.zeros(2), 0)
     assert ei.value.code == binding.SURV_E_INVALID
+
+
+def test_noalloc_rejects_malformed_col_ptr_on_the_host(lib):
+    # col_ptr is copied to the host and checked before any kernel reads
+    # row_idx through it.  Both malformed tables below stay inside the
+    # arrays' bounds, so no access could leave them even without the check.
+    import torch
+    n = 64
+    t = torch.arange(n, 0, -1, dtype=torch.int32).cuda()
+    s = torch.ones(n, dtype=torch.int8).cuda()
+    ri = torch.tensor([1, 4, 9, 2, 3, 7, 8, 11], dtype=torch.int32).cuda()
+    for cp in ([2, 5, 8], [0, 5, 3]):                       # col_ptr[0] != 0; decreasing
+        d = binding.SurvData(t, s, col_ptr=torch.tensor(cp, dtype=torch.int64).cuda(), row_idx=ri)
+        with pytest.raises(binding.SurvError) as ei:
+            binding.loglik_grad_hess_noalloc(d, "cox", np.zeros(2), 0)
+        assert ei.value.code == binding.SURV_E_INDEX
+    good = binding.SurvData(t, s, col_ptr=torch.tensor([0, 5, 8], dtype=torch.int64).cuda(), row_idx=ri)
+    _close(binding.loglik_grad_hess_noalloc(good, "cox", np.zeros(2), 1),
+           binding.loglik_grad_hess(good, "cox", np.zeros(2), 1))
