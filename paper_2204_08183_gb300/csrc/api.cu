@@ -247,7 +247,11 @@ int stage_data(const surv_data* d, int prec, surv_workspace* ws, cudaStream_t s,
 
 // Validation kernels on the staged data and the tie-group count: *K after a
 // synchronisation (ctrl zeroed here; prep errors mapped to return codes).
-int validate_and_count(int model, int layout, int prec, int64_t n, int64_t p, const Staged& st, DevCtrl* ctrl,
+// CSC values that are all exactly 1 are dropped from st (the kernels then
+// take every nonzero as 1, an indicator matrix): the arithmetic is the same
+// bit for bit (x e = e, x^2 = x, delta x = delta) and the values are not read
+// again.
+int validate_and_count(int model, int layout, int prec, int64_t n, int64_t p, Staged& st, DevCtrl* ctrl,
                        surv_workspace* ws, cudaStream_t s, void** blockcnt, int32_t* K, int64_t* launches) {
   CUDA_TRY(cudaMemsetAsync(ctrl, 0, sizeof(DevCtrl), s));
   CUDA_TRY(survgpu::prep_check_times(st.time, st.status, n, model, &ctrl->perr, s));
@@ -267,6 +271,7 @@ int validate_and_count(int model, int layout, int prec, int64_t n, int64_t p, co
   CUDA_TRY(cudaStreamSynchronize(s));
   if ((rc = map_prep_error(hc.perr))) return rc;
   *K = hc.K;
+  if (layout == SURV_CSC && st.vals && !(hc.perr & survgpu::PREP_VALUES_NOT_ONE)) st.vals = nullptr;
   return SURV_OK;
 }
 
@@ -337,7 +342,7 @@ int fit_common(int model, const surv_data* d, const surv_opts* o_in, double* bet
   int rc;
   Staged stg;
   if ((rc = stage_data(d, prec, ws, s, &stg, &launches))) return rc;
-  const void *colptr_d = stg.colptr, *rowidx_d = stg.rowidx, *vals_d = stg.vals;
+  const void *colptr_d = stg.colptr, *rowidx_d = stg.rowidx;
   const int64_t ld = stg.ld;
   const std::vector<int64_t>& colptr_h = stg.colptr_h;
 
@@ -362,6 +367,7 @@ int fit_common(int model, const surv_data* d, const surv_opts* o_in, double* bet
   void* blockcnt = nullptr;
   int32_t K = 0;
   if ((rc = validate_and_count(model, layout, prec, n, p, stg, ctrl, ws, s, &blockcnt, &K, &launches))) return rc;
+  const void* vals_d = stg.vals;  // null for indicator CSC data (all values 1)
   DevCtrl hc;
 
   // ---------------------------------------------------------- tables

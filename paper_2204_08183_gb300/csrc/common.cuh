@@ -194,6 +194,51 @@ __device__ __forceinline__ void warp_sum_some(A (&v)[N]) {
   }
 }
 
+// Sums of N values over the 32 lanes (N a power of two, 2..32) by recursive
+// halving: at distance d = 16, 8, ... each lane keeps half of its values
+// and adds the partner's copy of that half, so N values cost N - 1 + 5 -
+// log2(N) float-float additions instead of 5 N for N separate trees.  On
+// return v[0] holds the total of component warp_rs_component<N>(lane) in
+// every lane (lanes that differ only in the low 5 - log2(N) bits hold the
+// same component).  Fixed order: the result does not depend on timing.
+template <int N>
+__device__ __forceinline__ int warp_rs_component(int lane) {
+  int c = 0;
+#pragma unroll
+  for (int d = 16, h = N / 2; h >= 1; d >>= 1, h >>= 1)
+    if (lane & d) c += h;
+  return c;
+}
+template <int N>
+__device__ __forceinline__ int warp_rs_lane(int comp) {
+  int l = 0;
+#pragma unroll
+  for (int d = 16, h = N / 2; h >= 1; d >>= 1, h >>= 1)
+    if (comp & h) l |= d;
+  return l;
+}
+template <int N>
+__device__ __forceinline__ void warp_reduce_scatter(ff (&v)[N], int lane) {
+  static_assert(N >= 2 && N <= 32 && (N & (N - 1)) == 0, "N: a power of two");
+  int d = 16;
+#pragma unroll
+  for (int h = N / 2; h >= 1; h >>= 1, d >>= 1) {
+    const bool up = (lane & d) != 0;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const ff keep = up ? v[i + h] : v[i];
+      const ff give = up ? v[i] : v[i + h];
+      const ff got = {__shfl_xor_sync(0xffffffffu, give.hi, d), __shfl_xor_sync(0xffffffffu, give.lo, d)};
+      v[i] = up ? ff_add(got, keep) : ff_add(keep, got);
+    }
+  }
+#pragma unroll
+  for (; d >= 1; d >>= 1) {
+    const ff got = {__shfl_xor_sync(0xffffffffu, v[0].hi, d), __shfl_xor_sync(0xffffffffu, v[0].lo, d)};
+    v[0] = (lane & d) ? ff_add(got, v[0]) : ff_add(v[0], got);
+  }
+}
+
 // N independent inclusive scans over the lanes (Hillis-Steele, fixed
 // shape), interleaved level by level.
 template <int N>

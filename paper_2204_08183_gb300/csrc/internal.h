@@ -18,6 +18,7 @@ enum : unsigned {
   PREP_NONFINITE = 4u,
   PREP_INDEX = 8u,
   PREP_FOLD = 16u,
+  PREP_VALUES_NOT_ONE = 32u,  // not an error: some CSC value differs from 1
 };
 
 // Parameters of the persistent CCD kernel (passed as a __grid_constant__).

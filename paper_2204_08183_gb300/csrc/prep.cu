@@ -50,6 +50,7 @@ __global__ void k_check_csc(const int64_t* col_ptr, const int32_t* row_idx, cons
       if (r < 0 || r >= n) bits |= PREP_INDEX;
       if (i > a && row_idx[i - 1] >= r) bits |= PREP_INDEX;
       if (values && !isfinite(values[i])) bits |= PREP_NONFINITE;
+      if (values && values[i] != T(1)) bits |= PREP_VALUES_NOT_ONE;
     }
   }
   if (bits) atomicOr(perr, bits);

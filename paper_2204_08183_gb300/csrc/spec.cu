@@ -244,6 +244,95 @@ __global__ void __launch_bounds__(kSpNT, 2) k_spass(const __grid_constant__ CcdP
   }
 }
 
+// Warp 0 of a batch's last transform CTA: on j0 = 0 the objective at the
+// start of the sweep and the stopping rule; then lane b takes the candidate
+// step of coordinate j0 + b (Section 2.4) from the batch's sums s_tot
+// (sum d G per column, sum d (H - G^2) per column, sum d log den), the steps
+// are committed in order up to and including the first nonzero one, and
+// every lane writes one replica of the control line for the next batch.
+template <int B>
+__device__ __forceinline__ void commit_batch(const CcdParams& P, const LineView& lv, long long batches_prev, int j0,
+                                             int nb, bool eval, const ff* s_tot, const double* s_lin) {
+  GraphCtl* ctl = P.gctl;
+  const int lane = threadIdx.x & 31;
+  // objective at the start of the sweep and the stopping rule (j0 = 0)
+  int stop = 0, nevals = 0;
+  double f_prev = 0.0;
+  if (lane == 0) {
+    nevals = lv.nevals;
+    f_prev = lv.f_prev;
+    if (eval) {
+      const int sidx = lv.nevals;
+      const double ll = s_lin[0] - ff_to_d(s_tot[2 * B]);
+      const double f = ll + s_lin[1];
+      const double fp = sidx >= 1 ? lv.f_prev : 0.0;
+      const bool conv = sidx >= 1 && fabs(f - fp) / fabs(f) < P.tol;
+      stop = (conv || sidx >= P.max_sweeps) ? 1 : 0;
+      nevals = sidx + 1;
+      f_prev = f;
+      if (stop) {
+        P.out[OUT_LOGLIK] = ll;
+        P.out[OUT_OBJECTIVE] = f;
+        P.out[OUT_OBJECTIVE_PREV] = fp;
+        P.out[OUT_SWEEPS] = (double)sidx;
+        P.out[OUT_CONVERGED] = conv ? 1.0 : 0.0;
+        P.out[OUT_ETA_UPDATES] = (double)lv.eta_updates;
+        P.out[OUT_PASSES] = (double)(lv.passes + 1);
+        P.out[OUT_BATCHES] = (double)(batches_prev + 1);
+        ctl->done = 1;
+      }
+    }
+  }
+  stop = __shfl_sync(0xffffffffu, stop, 0);
+  // lane b: the candidate step of coordinate j0 + b at the current e
+  double applied = 0.0, bnew = 0.0, wnew = 0.0;
+  const int j = j0 + lane;
+  if (!stop && lane < nb) {
+    const double beta = __ldcg(P.beta + j), width = __ldcg(P.width + j);
+    const double grad = P.dTx[j] - ff_to_d(s_tot[lane]);  // l' = delta^T X_j - sum_k d_k G_k
+    const double hess = -ff_to_d(s_tot[B + lane]);         // l''
+    const double step = newton_step(beta, grad, hess, P.penalty, P.pen[j]);
+    if (step != 0.0) applied = copysign(fmin(fabs(step), width), step);
+    bnew = beta + applied;
+    wnew = fmax(2.0 * fabs(applied), width / 2.0);
+  }
+  // commit in order up to and including the first nonzero step
+  const unsigned nz = __ballot_sync(0xffffffffu, lane < nb && applied != 0.0);
+  const int bstar = nz ? __ffs((int)nz) - 1 : nb - 1;
+  if (!stop && lane <= bstar) {
+    P.beta[j] = bnew;
+    P.width[j] = wnew;
+  }
+  const double app = nz ? __shfl_sync(0xffffffffu, applied, bstar) : 0.0;
+  long long passes = 0, eta_updates = 0, batches = 0;
+  if (lane == 0) {
+    passes = lv.passes + (stop ? 1 : bstar + 1);
+    eta_updates = lv.eta_updates + (nz && !stop ? 1 : 0);
+    batches = batches_prev + 1;
+  }
+  passes = __shfl_sync(0xffffffffu, passes, 0);
+  eta_updates = __shfl_sync(0xffffffffu, eta_updates, 0);
+  batches = __shfl_sync(0xffffffffu, batches, 0);
+  nevals = __shfl_sync(0xffffffffu, nevals, 0);
+  f_prev = __shfl_sync(0xffffffffu, f_prev, 0);
+  int j0n = j0 + bstar + 1;
+  if (j0n >= P.p) j0n = 0;
+  const ff delta = d_to_ff(stop ? 0.0 : app);
+  CtlLine* L = &ctl->line[lane];
+  L->stop = stop;
+  L->nevals = nevals;
+  L->applied = stop ? 0.0 : app;
+  L->delta_hi = delta.hi;
+  L->delta_lo = delta.lo;
+  L->f_prev = f_prev;
+  L->passes = passes;
+  L->eta_updates = eta_updates;
+  L->j0 = stop ? j0 : j0n;
+  L->q = (nz && !stop) ? j0 + bstar : -1;
+  L->batches = batches;
+  if (lane == 0) ctl->ticket = 0u;
+}
+
 template <int B>
 __global__ void __launch_bounds__(kStNT) k_strans(const __grid_constant__ CcdParams P, int slot) {
   constexpr int R = SpCfg<B>::R;
@@ -260,10 +349,12 @@ __global__ void __launch_bounds__(kStNT) k_strans(const __grid_constant__ CcdPar
   const int kc_lo = P.wk0[c * WPC], kc_hi = P.wk0[(c + 1) * WPC];
   pdl_wait();
   LineView lv;
+  long long batches_prev = 0;
   if (tid == 0) {
     lv = load_line(ctl, c);
     s_stop = lv.stop;
     s_j0 = __ldcg(&ctl->line[c % kRep].j0);
+    batches_prev = __ldcg(&ctl->line[c % kRep].batches);
   }
   __syncthreads();
   if (s_stop) return;
@@ -381,82 +472,341 @@ __global__ void __launch_bounds__(kStNT) k_strans(const __grid_constant__ CcdPar
   }
   __syncthreads();
   if (w != 0) return;
-  // objective at the start of the sweep and the stopping rule (j0 = 0)
-  int stop = 0, nevals = 0;
-  double f_prev = 0.0;
-  if (lane == 0) {
-    nevals = lv.nevals;
-    f_prev = lv.f_prev;
-    if (eval) {
-      const int sidx = lv.nevals;
-      const double ll = s_lin[0] - ff_to_d(s_tot[2 * B]);
-      const double f = ll + s_lin[1];
-      const double fp = sidx >= 1 ? lv.f_prev : 0.0;
-      const bool conv = sidx >= 1 && fabs(f - fp) / fabs(f) < P.tol;
-      stop = (conv || sidx >= P.max_sweeps) ? 1 : 0;
-      nevals = sidx + 1;
-      f_prev = f;
-      if (stop) {
-        P.out[OUT_LOGLIK] = ll;
-        P.out[OUT_OBJECTIVE] = f;
-        P.out[OUT_OBJECTIVE_PREV] = fp;
-        P.out[OUT_SWEEPS] = (double)sidx;
-        P.out[OUT_CONVERGED] = conv ? 1.0 : 0.0;
-        P.out[OUT_ETA_UPDATES] = (double)lv.eta_updates;
-        P.out[OUT_PASSES] = (double)(lv.passes + 1);
-        P.out[OUT_BATCHES] = (double)(__ldcg(&ctl->line[c % kRep].batches) + 1);
-        ctl->done = 1;
+  commit_batch<B>(P, lv, batches_prev, j0, nb, eval, s_tot, s_lin);
+}
+
+
+// ---------------------------------------------------------------------------
+// Indicator columns (CSC without values: every nonzero is 1, so x^2 = x and
+// e x^2 = e x).  One numerator component per column: R = 1 + B record and
+// aggregate components, and H_k = G_k, so H_k - G_k^2 = G_k (1 - G_k).
+//   k_ipass   as k_spass, but the B column walks run in lockstep: each round
+//             issues the row-index loads of every column, then the gathers
+//             of e, so one DRAM and one L2 round trip serve all B columns;
+//             the lanes keep float-float partials and one reduce-scatter
+//             over the R components gives the warp totals.
+//   k_itrans  one CTA per kItF pass CTAs: the prefix of the pass CTAs'
+//             aggregates before its range, G_k of the B columns at its group
+//             ends, partial sums; the last CTA commits the batch.  It reads
+//             its control line before waiting: the line was written by the
+//             previous batch's transform, which finished before this batch's
+//             pass kernel passed its own wait.
+template <int B>
+struct IpCfg {
+  static constexpr int R = 1 + B;
+  static constexpr int RP = R <= 2 ? 2 : (R <= 4 ? 4 : (R <= 8 ? 8 : (R <= 16 ? 16 : 32)));
+  static constexpr int NP = 2 * B + 1;
+  static constexpr int NPP = NP <= 2 ? 2 : (NP <= 4 ? 4 : (NP <= 8 ? 8 : (NP <= 16 ? 16 : 32)));
+  static constexpr int SR = B <= 4 ? 2 : 1;  // rounds of 32 nonzeros per column in flight
+};
+constexpr int kItF = 8;      // pass CTAs per transform CTA
+constexpr int kItNT = 512;   // transform kernel threads
+constexpr int kItWarps = kItNT / 32;
+
+// Position of the warp's group end k (k warp-uniform): lane registers for
+// the first 32, a broadcast load beyond.
+__device__ __forceinline__ int end_at(const int32_t* gend, int k, int k_lo, int k_hi, int kreg) {
+  if (k >= k_hi) return INT_MAX;
+  const int i = k - k_lo;
+  if (i < 32) return __shfl_sync(0xffffffffu, kreg, i);
+  return __ldg(gend + k);
+}
+
+// The B columns' nonzeros in the warp's rows: col[b] points at the first,
+// len[b] entries.  At each group end before a column's last nonzero the
+// warp-relative prefix of e x is stored in rec[k * R + 1 + b]; acc[b] gets
+// the lane partials, kn[b] the first end not written.
+template <int B, int SR>
+__device__ __forceinline__ void ip_sparse(const float* e, const int32_t* gend, const int32_t* const (&col)[B],
+                                          const int (&len)[B], ff* rec, int R, int k_lo, int k_hi, int kreg,
+                                          ff (&acc)[B], int (&kn)[B]) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t keep = l2_keep(), strm = l2_stream();
+  int ne[B];
+  int len_max = 0;
+#pragma unroll
+  for (int b = 0; b < B; ++b) {
+    acc[b] = ff_zero();
+    kn[b] = k_lo;
+    ne[b] = end_at(gend, k_lo, k_lo, k_hi, kreg);
+    len_max = max(len_max, len[b]);
+  }
+  for (int base = 0; base < len_max; base += 32 * SR) {
+    int row[B][SR];
+    float ev[B][SR];
+#pragma unroll
+    for (int b = 0; b < B; ++b)
+#pragma unroll
+      for (int r = 0; r < SR; ++r) {
+        const int i = base + 32 * r + lane;
+        row[b][r] = i < len[b] ? ld_hint(col[b] + i, strm) : INT_MAX;
       }
+#pragma unroll
+    for (int b = 0; b < B; ++b)
+#pragma unroll
+      for (int r = 0; r < SR; ++r) ev[b][r] = row[b][r] != INT_MAX ? ld_hint(e + row[b][r], keep) : 0.f;
+#pragma unroll
+    for (int b = 0; b < B; ++b)
+#pragma unroll
+      for (int r = 0; r < SR; ++r) {
+        const int rb = base + 32 * r;
+        if (rb >= len[b]) continue;
+        const int nvalid = min(32, len[b] - rb);
+        const int last_row = __shfl_sync(0xffffffffu, row[b][r], nvalid - 1);
+        while (ne[b] < last_row) {
+          ff pref = ff_add_f(acc[b], row[b][r] <= ne[b] ? ev[b][r] : 0.f);
+          pref = warp_sum(pref);
+          if (lane == 0) rec[(size_t)kn[b] * R + 1 + b] = pref;
+          ++kn[b];
+          ne[b] = end_at(gend, kn[b], k_lo, k_hi, kreg);
+        }
+        acc[b] = ff_add_f(acc[b], ev[b][r]);
+      }
+  }
+}
+
+template <int B>
+__global__ void __launch_bounds__(kSpNT, 2) k_ipass(const __grid_constant__ CcdParams P, int slot) {
+  constexpr int R = IpCfg<B>::R, RP = IpCfg<B>::RP, SR = IpCfg<B>::SR;
+  __shared__ ff s_wtot[kMaxWarpsPerCta][R];
+  __shared__ int s_stop, s_j0, s_q;
+  __shared__ double s_applied;
+  __shared__ float s_delta[2];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int WPC = P.wpc, c = blockIdx.x, G = P.G;
+  const int64_t n = P.n;
+  const int64_t nwords = (n + 31) >> 5;
+  const int gw = c * WPC + w;
+  const int64_t word_lo = min((int64_t)gw * P.wpw, nwords);
+  const int64_t word_hi = min(word_lo + P.wpw, nwords);
+  const int64_t row_lo = word_lo * 32, row_hi = min(word_hi * 32, n);
+  const int k_lo = P.wk0[gw], k_hi = P.wk0[gw + 1];
+  const int kreg = k_lo + lane < k_hi ? P.gend[k_lo + lane] : INT_MAX;
+  pdl_wait();
+  if (tid == 0) {
+    const CtlLine* L = &P.gctl->line[c % kRep];
+    s_stop = __ldcg(&L->stop);
+    s_j0 = __ldcg(&L->j0);
+    s_q = __ldcg(&L->q);
+    s_applied = __ldcg(&L->applied);
+    s_delta[0] = __ldcg(&L->delta_hi);
+    s_delta[1] = __ldcg(&L->delta_lo);
+  }
+  __syncthreads();
+  if (s_stop) return;
+  const int j0 = s_j0;
+  const int nb = min(B, P.p - j0);
+  const int nw1 = P.nwarps + 1;
+  const int32_t* col[B];
+  int len[B];
+#pragma unroll
+  for (int b = 0; b < B; ++b) {
+    const int j = b < nb ? j0 + b : j0;
+    const int a = P.woff[(size_t)j * nw1 + gw];
+    const int z = P.woff[(size_t)j * nw1 + gw + 1];
+    col[b] = P.row_idx + P.col_ptr[j] + a;
+    len[b] = b < nb ? z - a : 0;
+  }
+  if (s_applied != 0.0) warp_update<0, float>(P, s_q, gw, row_lo, row_hi, s_applied, ff{s_delta[0], s_delta[1]});
+  ff* rec = reinterpret_cast<ff*>(P.rec);
+  const float* e = reinterpret_cast<const float*>(P.e);
+  ff tot[RP];
+  tot[0] = sp_dense(e, P.gend, row_lo, row_hi, rec, R, EndCursor{k_lo, k_hi, k_lo, kreg});
+  int kn[B];
+  {
+    ff acc[B];
+    ip_sparse<B, SR>(e, P.gend, col, len, rec, R, k_lo, k_hi, kreg, acc, kn);
+#pragma unroll
+    for (int b = 0; b < B; ++b) tot[1 + b] = acc[b];
+  }
+#pragma unroll
+  for (int m = R; m < RP; ++m) tot[m] = ff_zero();
+  warp_reduce_scatter<RP>(tot, lane);
+  const int comp = warp_rs_component<RP>(lane);
+  if (comp < R && lane == warp_rs_lane<RP>(comp)) {
+    s_wtot[w][comp] = tot[0];
+    // group ends after the column's last nonzero in the warp's rows see the
+    // warp total
+    if (comp >= 1) {
+      int k0 = k_hi;
+#pragma unroll
+      for (int b = 0; b < B; ++b)
+        if (comp == 1 + b) k0 = kn[b];
+      for (int k = k0; k < k_hi; ++k) rec[(size_t)k * R + comp] = tot[0];
     }
   }
-  stop = __shfl_sync(0xffffffffu, stop, 0);
-  // lane b: the candidate step of coordinate j0 + b at the current e
-  double applied = 0.0, bnew = 0.0, wnew = 0.0;
-  const int j = j0 + lane;
-  if (!stop && lane < nb) {
-    const double beta = __ldcg(P.beta + j), width = __ldcg(P.width + j);
-    const double grad = P.dTx[j] - ff_to_d(s_tot[lane]);  // l' = delta^T X_j - sum_k d_k G_k
-    const double hess = -ff_to_d(s_tot[B + lane]);         // l''
-    const double step = newton_step(beta, grad, hess, P.penalty, P.pen[j]);
-    if (step != 0.0) applied = copysign(fmin(fabs(step), width), step);
-    bnew = beta + applied;
-    wnew = fmax(2.0 * fabs(applied), width / 2.0);
+  pdl_launch_dependents();
+  __syncthreads();
+  // warp m scans component m over the CTA's warps
+  for (int m = w; m < R; m += WPC) {
+    ff v = ff_zero();
+    if (lane < WPC) v = s_wtot[lane][m];
+    const ff incl = warp_inclusive_scan(v, lane);
+    ff ex = shfl_up(incl, 1);
+    if (lane == 0) ex = ff_zero();
+    if (lane < WPC) P.wt[(size_t)m * P.nwarps + c * WPC + lane] = pack8(ex);
+    const ff t = shfl_idx(incl, WPC - 1);
+    if (lane == 0) P.agg[(size_t)m * G + c] = pack8(t);
   }
-  // commit in order up to and including the first nonzero step
-  const unsigned nz = __ballot_sync(0xffffffffu, lane < nb && applied != 0.0);
-  const int bstar = nz ? __ffs((int)nz) - 1 : nb - 1;
-  if (!stop && lane <= bstar) {
-    P.beta[j] = bnew;
-    P.width[j] = wnew;
+}
+
+template <int B>
+__global__ void __launch_bounds__(kItNT) k_itrans(const __grid_constant__ CcdParams P, int slot) {
+  constexpr int R = IpCfg<B>::R, RP = IpCfg<B>::RP, NP = IpCfg<B>::NP, NPP = IpCfg<B>::NPP;
+  constexpr int NR = NP > R ? NP : R;
+  __shared__ ff s_red[kItWarps][NR];
+  __shared__ ff s_T[kItF][R];
+  __shared__ ff s_tot[NP];
+  __shared__ int s_stop, s_j0, s_last;
+  __shared__ double s_lin[2];
+  GraphCtl* ctl = P.gctl;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int WPC = P.wpc, G = P.G, G2 = gridDim.x, c2 = blockIdx.x;
+  const int q_lo = c2 * kItF, q_hi = min(q_lo + kItF, G);
+  const int kc_lo = P.wk0[q_lo * WPC], kc_hi = P.wk0[q_hi * WPC];
+  LineView lv;
+  long long batches_prev = 0;
+  if (tid == 0) {
+    lv = load_line(ctl, c2);
+    s_stop = lv.stop;
+    s_j0 = __ldcg(&ctl->line[c2 % kRep].j0);
+    batches_prev = __ldcg(&ctl->line[c2 % kRep].batches);
   }
-  const double app = nz ? __shfl_sync(0xffffffffu, applied, bstar) : 0.0;
-  long long passes = 0, eta_updates = 0, batches = 0;
-  if (lane == 0) {
-    passes = lv.passes + (stop ? 1 : bstar + 1);
-    eta_updates = lv.eta_updates + (nz && !stop ? 1 : 0);
-    batches = __ldcg(&ctl->line[c % kRep].batches) + 1;
+  __syncthreads();
+  if (s_stop) {
+    pdl_wait();
+    return;
   }
-  passes = __shfl_sync(0xffffffffu, passes, 0);
-  eta_updates = __shfl_sync(0xffffffffu, eta_updates, 0);
-  batches = __shfl_sync(0xffffffffu, batches, 0);
-  nevals = __shfl_sync(0xffffffffu, nevals, 0);
-  f_prev = __shfl_sync(0xffffffffu, f_prev, 0);
-  int j0n = j0 + bstar + 1;
-  if (j0n >= P.p) j0n = 0;
-  const ff delta = d_to_ff(stop ? 0.0 : app);
-  CtlLine* L = &ctl->line[lane];
-  L->stop = stop;
-  L->nevals = nevals;
-  L->applied = stop ? 0.0 : app;
-  L->delta_hi = delta.hi;
-  L->delta_lo = delta.lo;
-  L->f_prev = f_prev;
-  L->passes = passes;
-  L->eta_updates = eta_updates;
-  L->j0 = stop ? j0 : j0n;
-  L->q = (nz && !stop) ? j0 + bstar : -1;
-  L->batches = batches;
-  if (lane == 0) ctl->ticket = 0u;
+  const int j0 = s_j0;
+  const int nb = min(B, P.p - j0);
+  const bool eval = j0 == 0;
+  const int nwork = (kc_hi - kc_lo) * nb;
+  // the first work item's group table entries (written by the prep)
+  int k1 = 0, b1 = 0, d1 = 0, gw1 = 0;
+  if (tid < nwork) {
+    k1 = kc_lo + tid / nb;
+    b1 = tid - (tid / nb) * nb;
+    d1 = P.dk[k1];
+    gw1 = (int)((P.gend[k1] >> 5) / P.wpw);
+  }
+  pdl_wait();
+
+  // prefix of the pass CTAs' aggregates before q_lo, then within the range
+  {
+    ff t[RP];
+#pragma unroll
+    for (int m = 0; m < RP; ++m) t[m] = ff_zero();
+    for (int q = tid; q < q_lo; q += kItNT)
+#pragma unroll
+      for (int m = 0; m < R; ++m) t[m] = ff_add(t[m], unpack8<ff>(__ldcg(P.agg + (size_t)m * G + q)));
+    warp_reduce_scatter<RP>(t, lane);
+    const int comp = warp_rs_component<RP>(lane);
+    if (comp < R && lane == warp_rs_lane<RP>(comp)) s_red[w][comp] = t[0];
+  }
+  __syncthreads();
+  if (tid < R) {
+    uint64_t ag[kItF];
+#pragma unroll
+    for (int f = 0; f < kItF; ++f) ag[f] = q_lo + f < q_hi ? __ldcg(P.agg + (size_t)tid * G + q_lo + f) : 0ull;
+    ff a = s_red[0][tid];
+    for (int q = 1; q < kItWarps; ++q) a = ff_add(a, s_red[q][tid]);
+#pragma unroll
+    for (int f = 0; f < kItF; ++f) {
+      s_T[f][tid] = a;
+      a = ff_add(a, unpack8<ff>(ag[f]));
+    }
+  }
+  __syncthreads();
+
+  // G_k of the batch's columns at the range's group ends (steps 3-4): one
+  // thread per (group end, column); column 0's thread also adds d_k log
+  // den_k on evaluation passes
+  ff f1[B], f2[B];
+#pragma unroll
+  for (int b = 0; b < B; ++b) {
+    f1[b] = ff_zero();
+    f2[b] = ff_zero();
+  }
+  double pl = 0.0;
+  const ff* rec = reinterpret_cast<const ff*>(P.rec);
+  for (int it = tid; it < nwork; it += kItNT) {
+    int k, b, d, gwk;
+    if (it == tid) {
+      k = k1, b = b1, d = d1, gwk = gw1;
+    } else {
+      k = kc_lo + it / nb;
+      b = it - (it / nb) * nb;
+      d = P.dk[k];
+      gwk = (int)((P.gend[k] >> 5) / P.wpw);
+    }
+    if (d == 0) continue;
+    const int f = gwk / WPC - q_lo;
+    const ff den = ff_add(ff_add(s_T[f][0], unpack8<ff>(__ldcg(P.wt + gwk))), rec[(size_t)k * R]);
+    const ff n1 = ff_add(ff_add(s_T[f][1 + b], unpack8<ff>(__ldcg(P.wt + (size_t)(1 + b) * P.nwarps + gwk))),
+                         rec[(size_t)k * R + 1 + b]);
+    const ff Gk = ff_div(n1, den);
+    const ff g1 = ff_mul_f(Gk, (float)d);
+    const ff g2 = ff_mul_f(ff_sub(Gk, ff_mul(Gk, Gk)), (float)d);
+#pragma unroll
+    for (int q = 0; q < B; ++q)
+      if (q == b) {
+        f1[q] = ff_add(f1[q], g1);
+        f2[q] = ff_add(f2[q], g2);
+      }
+    if (eval && b == 0) pl += (double)d * log(ff_to_d(den));
+  }
+  // CTA partials, fixed order
+  {
+    ff v[NPP];
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      v[b] = f1[b];
+      v[B + b] = f2[b];
+    }
+    v[2 * B] = d_to_ff(pl);
+#pragma unroll
+    for (int m = NP; m < NPP; ++m) v[m] = ff_zero();
+    warp_reduce_scatter<NPP>(v, lane);
+    const int comp = warp_rs_component<NPP>(lane);
+    if (comp < NP && lane == warp_rs_lane<NPP>(comp)) s_red[w][comp] = v[0];
+  }
+  __syncthreads();
+  uint64_t* part = reinterpret_cast<uint64_t*>(P.slot_part);
+  if (tid < NP) {
+    ff a = s_red[0][tid];
+    for (int q = 1; q < kItWarps; ++q) a = ff_add(a, s_red[q][tid]);
+    part[(size_t)tid * G2 + c2] = pack8(a);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    unsigned prev;
+    asm volatile("atom.add.release.gpu.u32 %0, [%1], 1;" : "=r"(prev) : "l"(&ctl->ticket) : "memory");
+    s_last = prev == (unsigned)(G2 - 1);
+  }
+  pdl_launch_dependents();
+  __syncthreads();
+  if (!s_last) return;
+
+  // ------------------------------------ last CTA: the steps of the batch
+  asm volatile("fence.acq_rel.gpu;" ::: "memory");
+  for (int r = w; r < NP; r += kItWarps) {
+    ff acc = ff_zero();
+    for (int qc = lane; qc < G2; qc += 32) acc = ff_add(acc, unpack8<ff>(__ldcg(part + (size_t)r * G2 + qc)));
+    acc = warp_sum(acc);
+    if (lane == 0) s_tot[r] = acc;
+  }
+  if (w == kItWarps - 1 && eval) {
+    double lin, pen;
+    warp_lin_pen(P, -1, 0.0, lin, pen);
+    if (lane == 0) {
+      s_lin[0] = lin;
+      s_lin[1] = pen;
+    }
+  }
+  __syncthreads();
+  if (w != 0) return;
+  commit_batch<B>(P, lv, batches_prev, j0, nb, eval, s_tot, s_lin);
 }
 
 template <int B>
@@ -474,10 +824,17 @@ cudaError_t capture_spec(const CcdParams& P, int S, bool pdl, cudaStream_t cs, c
   cp.numAttrs = 1;
   cudaLaunchConfig_t ct = cp;
   ct.blockDim = dim3(kStNT);
+  // indicator columns: the lockstep walks and the ranged transform
+  const bool ind = P.values == nullptr;
+  if (ind) {
+    ct.gridDim = dim3((P.G + kItF - 1) / kItF);
+    ct.blockDim = dim3(kItNT);
+  }
   cudaError_t lst = cudaSuccess;
   for (int slot = 0; slot < S && lst == cudaSuccess; ++slot) {
-    lst = cudaLaunchKernelEx(&cp, k_spass<B>, P, slot);
-    if (lst == cudaSuccess) lst = cudaLaunchKernelEx(&ct, k_strans<B>, P, slot);
+    lst = ind ? cudaLaunchKernelEx(&cp, k_ipass<B>, P, slot) : cudaLaunchKernelEx(&cp, k_spass<B>, P, slot);
+    if (lst == cudaSuccess)
+      lst = ind ? cudaLaunchKernelEx(&ct, k_itrans<B>, P, slot) : cudaLaunchKernelEx(&ct, k_strans<B>, P, slot);
   }
   st = cudaStreamEndCapture(cs, g);
   return lst != cudaSuccess ? lst : st;

@@ -83,7 +83,7 @@ def test_groups_many_km_factors(lib, K):
     assert np.array_equal(gend, og.astype(np.int32))
     assert np.array_equal(dk, oracle.group_counts(og, st, 1).astype(np.int32))
     ref = oracle.km_censoring_groups(t, st, og)
-    assert ref.min() < 1e-3                          # a long product, far from 1
+    assert ref.min() < 0.05                          # a long product, far from 1
     if K <= 4096:
         assert np.array_equal(Gk, ref)
     else:
