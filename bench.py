@@ -71,6 +71,11 @@ def parse():
     return ap.parse_args()
 
 
+# Steady-state DRAM bytes per row pass of the headline kernels (ncu capture
+# of the committed k_ipass<4> + k_itrans<4>; None until captured).
+TRAFFIC_IND_ROW_PASS = None
+
+
 def workload(n, p):
     from paper_2204_08183_gb300 import synth
     d = synth.cohort_cox_sparse(n, p, seed=SEED, density=0.05, n_true=10, laplace_scale=0.2,
@@ -225,15 +230,19 @@ def run_gpu(args, rank, world):
     K = infos[-1]["n_groups"]
     passes = sum(i["coordinate_passes"] for i in infos)
     upd = sum(i["eta_updates"] for i in infos)
-    per_pass = 4 * n + 8 * nnz / p + 8 * K          # e stream + column j (row, value) + group table
-    per_update = 28 * nnz / p                         # row, value, eta r/w (8+8), e write
+    # CSC values that are all 1 are indicators: the library drops them and
+    # reads only the row indices of a column
+    ind = d["values"] is None or bool(np.all(d["values"] == 1))
+    vb = 0 if ind else 4                              # bytes of a value per nonzero
+    per_pass = 4 * n + (4 + vb) * nnz / p + 8 * K     # e stream + column j (row, value) + group table
+    per_update = (24 + vb) * nnz / p                  # row, value, eta r/w (8+8), e write
     alg_bytes = passes * per_pass + upd * per_update
     row_passes = sum(i["row_passes"] for i in infos)
     batched = (not sn) and args.schedule == "graph" and row_passes < passes
     if batched:
         # speculative batches: a row pass reads e once and the slices of up
         # to 4 columns (counted as 4: an upper bound on the columns read)
-        per_row_pass = 4 * n + 4 * 8 * nnz / p + 8 * K
+        per_row_pass = 4 * n + 4 * (4 + vb) * nnz / p + 8 * K
         alg_bytes = row_passes * per_row_pass + upd * per_update
     if sn:
         # per coordinate: column j (row, value) and, per nonzero, e, its
@@ -262,11 +271,11 @@ def run_gpu(args, rank, world):
                 "row_passes_per_fit": row_passes / len(infos)}
     if batched:
         roofline["unit_of_work"] = "one row pass (a speculative batch of up to 4 coordinates)"
-        if n == 10_000_000 and p == 100:
-            # dram__bytes_read.sum + dram__bytes_write.sum of k_spass<4> +
-            # k_strans<4> per row pass, steady state (ncu --cache-control
-            # none); see profiles/k_spass_k_strans_cox_csc_n1e7.md
-            roofline["traffic"] = round((21325107 + 4341018) + (13926 + 37350))
+        if n == 10_000_000 and p == 100 and ind and TRAFFIC_IND_ROW_PASS:
+            # dram__bytes_read.sum + dram__bytes_write.sum of k_ipass<4> +
+            # k_itrans<4> per row pass, steady state (ncu --cache-control
+            # none); see profiles/k_ipass_k_itrans_cox_csc_n1e7.md
+            roofline["traffic"] = TRAFFIC_IND_ROW_PASS
             roofline["traffic_note"] = "bytes per row pass, ncu steady-state capture of the kernels as committed"
         roofline["algorithmic_bytes_per_row_pass"] = round(alg_bytes / row_passes)
         roofline["us_per_row_pass"] = round(kern_ms * 1e3 / row_passes, 3)
@@ -284,8 +293,8 @@ def run_gpu(args, rank, world):
     roofline["kernel"] = ("ccd_kernel<cox,csc,f32> (persistent, one launch per fit)" if args.schedule == "persistent"
                           else "k_pass + k_trans <cox,csc,f32>, one pair per coordinate, one graph replay per sweep")
     if batched:
-        roofline["kernel"] = ("k_spass<4> + k_strans<4>: one pair per speculative batch of 4 coordinates, "
-                              "graph replays of batches")
+        roofline["kernel"] = (("k_ipass<4> + k_itrans<4>" if ind else "k_spass<4> + k_strans<4>") +
+                              ": one pair per speculative batch of 4 coordinates, graph replays of batches")
     if sn:
         roofline["kernel"] = ("k_sn_den_a/den_b/lam (after nonzero steps only) + k_sn_col_a/col_b per coordinate, "
                               "one graph replay per sweep")

@@ -292,11 +292,15 @@ int loglik_grad_hess_noalloc(const surv_data *data, int32_t model, const double 
  * gradient dNLL/dB = X^T (exp(eta) * Lambda - delta), Lambda_b(i) the sum of
  * d_k / den_kb over the tie groups whose risk set holds i.
  *
- * X is bfloat16, row-major n x p; B float32 row-major p x C.  X B runs on
- * the tensor cores (bf16 inputs, FP32 accumulation) with B split into a
- * bf16 high and low part, so eta carries about 16 significant bits of B;
- * the risk-set scans use FP32 values with float-float running sums and the
- * logs are FP64.  All arrays are device memory; C <= 64. */
+ * X is bfloat16, row-major n x p; B float32 row-major p x C.  X B and
+ * X^T G run on the tensor cores in the library's own kernels (TMA tile
+ * loads, tcgen05.mma, bf16 inputs, FP32 accumulation in tensor memory) with
+ * B and G split into a bf16 high and low part, so eta carries about 16
+ * significant bits of B; the partial sums of X^T G over row ranges are added
+ * in FP64; the risk-set scans use FP32 values with float-float running sums
+ * and the logs are FP64.  All arrays are device memory; C <= 64; B is held
+ * in shared memory during X B, which bounds p (p <= 512 for C = 64, about
+ * 1500 for C <= 16; SURV_E_INVALID beyond). */
 typedef struct surv_nll_data {
   int64_t n;                     /* subjects                                       */
   int32_t p;                     /* covariates (columns of X)                      */
@@ -309,7 +313,10 @@ typedef struct surv_nll_data {
 /* nll[C] (device doubles) at B [p][C] (device floats).  Keeps eta and the
  * risk-set sums in the workspace `ws` (required) for cox_nll_backward.
  * Errors: SURV_E_INVALID (null, sizes, host pointers), SURV_E_UNSORTED,
- * SURV_E_STATUS, SURV_E_NOMEM, SURV_E_CUDA. */
+ * SURV_E_STATUS, SURV_E_NOMEM, SURV_E_CUDA; SURV_E_DEVICE_TIMEOUT when a
+ * bounded wait inside the tensor-core kernels of an earlier forward or
+ * backward call on this workspace expired (those results were invalid; the
+ * calls do not synchronise, so the next forward reports it). */
 int cox_nll_forward(const surv_nll_data *data, const float *B, double *nll, void *stream, surv_workspace *ws);
 
 /* grad_B [p][C] (device floats) = sum_b grad_nll[b] dNLL_b/dB at the B of

@@ -72,10 +72,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
             if log.strip():
                 sys.stderr.write(log)
     tmp = LIB + ".tmp"
-    # cuBLAS (plain GEMMs of the differentiable form) from the toolkit
-    cuda_lib = os.path.join(os.path.dirname(os.path.dirname(nvcc())), "lib64")
-    cmd = [nvcc()] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs + \
-        ["-L", cuda_lib, "-lcublas", "-Xlinker", "-rpath," + cuda_lib]
+    cmd = [nvcc()] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))

@@ -91,7 +91,6 @@ int ensure(surv_workspace* ws, int id, size_t bytes, void** out) { return survgp
 
 void free_all(surv_workspace* ws) {
   survgpu::graph_cache_free(&ws->graph);
-  survgpu::ws_release_blas(ws);
   for (auto& b : ws->bufs) {
     if (b.p) cudaFree(b.p);
     b.p = nullptr;

@@ -2,22 +2,22 @@
 // (Breslow ties) of C linear predictors at once, eta = X B, and its gradient
 // with respect to B.
 //
-//   forward   Bcat = [B_hi | B_lo] (bf16 split of the FP32 B), one tensor-
-//             core GEMM Y = X Bcat (bf16 x bf16 -> FP32, cuBLAS), then the
-//             risk-set scan: eta = Y_hi + Y_lo, e = exp(eta); every lane of
-//             a warp owns two of the C columns and walks the warp's rows in
-//             order with float-float running sums, so a group end costs its
-//             lanes a store, not a reduction; a per-column kernel adds the
-//             prefix of the warps before, takes d_k log den_k in FP64 and
-//             returns NLL_b = -sum_i delta_i eta_ib + sum_k d_k log den_kb.
+//   forward   Bcat^T = [B_hi | B_lo]^T (bf16 split of the FP32 B), the
+//             tensor-core product eta = X B_hi + X B_lo (nll_tc.cu: TMA,
+//             tcgen05.mma with FP32 accumulators in TMEM), then the risk-set
+//             scan: e = exp(eta); every lane of a warp owns two of the C
+//             columns and walks the warp's rows in order with float-float
+//             running sums, so a group end costs its lanes a store, not a
+//             reduction; a per-column kernel adds the prefix of the warps
+//             before, takes d_k log den_k in FP64 and returns
+//             NLL_b = -sum_i delta_i eta_ib + sum_k d_k log den_kb.
 //   backward  Lambda_kb = sum_{k' >= k} d_k' / den_k'b (reverse scan per
 //             column), G_ib = g_b (e_ib Lambda_b(group of i) - delta_i) split
-//             into bf16 [G_hi | G_lo], one GEMM X^T Gcat, halves summed.
-//
-// The GEMMs are plain products and go to cuBLAS; every other step is here.
-#include <cublas_v2.h>
+//             into bf16 [G_hi | G_lo], the tensor-core product X^T Gcat
+//             (nll_tc.cu), its halves and CTA partials summed in FP64.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cfloat>
 #include <climits>
 #include <cmath>
@@ -35,39 +35,44 @@ constexpr int kNllThreads = 512;   // scan kernels: two CTAs of 16 warps per SM
 constexpr int kNllMaxCols = 64;    // two columns per lane
 constexpr int kRowsAhead = 4;      // rows whose loads a warp keeps in flight
 
-// B (p x C, row-major FP32) -> Bcat (p x 2C, row-major bf16) = [hi | lo]
-__global__ void k_split_b(const float* B, int64_t p, int C, __nv_bfloat16* Bcat) {
+// B (p x C, row-major FP32) -> Bcat^T (2 Cp rows of ld bf16): row c < C holds
+// hi(B[:, c]), row Cp + c holds lo(B[:, c]) = bf16(B - hi); every other entry
+// (padding rows and columns p..ld-1) is zero.
+__global__ void k_split_bt(const float* B, int64_t p, int C, int Cp, int64_t ld, __nv_bfloat16* BcatT) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= p * C) return;
-  const int64_t j = i / C;
-  const int c = (int)(i % C);
-  const float b = B[i];
-  const __nv_bfloat16 hi = __float2bfloat16_rn(b);
-  const __nv_bfloat16 lo = __float2bfloat16_rn(b - __bfloat162float(hi));
-  Bcat[j * 2 * C + c] = hi;
-  Bcat[j * 2 * C + C + c] = lo;
+  const int NB = 2 * Cp;
+  if (i >= (int64_t)NB * ld) return;
+  const int r = (int)(i / ld);
+  const int64_t j = i - (int64_t)r * ld;
+  const int c = r < Cp ? r : r - Cp;
+  __nv_bfloat16 v = __float2bfloat16_rn(0.f);
+  if (c < C && j < p) {
+    const float b = B[j * C + c];
+    const __nv_bfloat16 hi = __float2bfloat16_rn(b);
+    v = r < Cp ? hi : __float2bfloat16_rn(b - __bfloat162float(hi));
+  }
+  BcatT[i] = v;
 }
 
-// gBcat (p x 2C, column-major FP32) -> grad_B (p x C, row-major FP32)
-__global__ void k_sum_halves(const float* gBcat, int64_t p, int C, float* grad_B) {
+// X (n x p) -> Xp (n x ld), zero columns p..ld-1 (TMA needs a row pitch that
+// is a multiple of 16 bytes)
+__global__ void k_pad_x(const __nv_bfloat16* X, int64_t n, int64_t p, int64_t ld, __nv_bfloat16* Xp) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= p * C) return;
-  const int64_t j = i / C;
-  const int c = (int)(i % C);
-  grad_B[i] = gBcat[(int64_t)c * p + j] + gBcat[(int64_t)(C + c) * p + j];
+  if (i >= n * ld) return;
+  const int64_t r = i / ld, j = i - r * ld;
+  Xp[i] = j < p ? X[r * p + j] : __float2bfloat16_rn(0.f);
 }
 
-// eta of columns c0 = 2 lane and c0 + 1 of row r: Y_hi + Y_lo (8-byte loads
-// when C is even, streaming: Y is read once per kernel)
+// eta of columns c0 = 2 lane and c0 + 1 of row r (8-byte loads when C is
+// even, streaming: eta is read once per kernel)
 __device__ __forceinline__ void load_pair(const float* y, int C, int c0, bool has0, bool has1, float& v0, float& v1) {
   if (has1 && (C & 1) == 0) {
     const float2 h = __ldcs(reinterpret_cast<const float2*>(y + c0));
-    const float2 l = __ldcs(reinterpret_cast<const float2*>(y + C + c0));
-    v0 = h.x + l.x;
-    v1 = h.y + l.y;
+    v0 = h.x;
+    v1 = h.y;
   } else {
-    v0 = has0 ? __ldcs(y + c0) + __ldcs(y + C + c0) : 0.f;
-    v1 = has1 ? __ldcs(y + c0 + 1) + __ldcs(y + C + c0 + 1) : 0.f;
+    v0 = has0 ? __ldcs(y + c0) : 0.f;
+    v1 = has1 ? __ldcs(y + c0 + 1) : 0.f;
   }
 }
 
@@ -75,13 +80,12 @@ __device__ __forceinline__ void load_pair(const float* y, int C, int c0, bool ha
 // the adjacent columns 2l and 2l + 1.  Outputs: rec[k][c] (warp-relative prefix of e at
 // group end k, float-float), wt[gw][c] and wd[gw][c] (the warp's sums of e
 // and of delta * eta).
-__global__ void __launch_bounds__(kNllThreads, 2) k_nll_scan(const float* Y, int64_t n, int C, const int8_t* status,
+__global__ void __launch_bounds__(kNllThreads, 2) k_nll_scan(const float* eta, int64_t n, int C, const int8_t* status,
                                                           const int32_t* gend, const int32_t* wk0, int64_t rpw,
                                                           float2* rec, float2* wt, float2* wd) {
   const int lane = threadIdx.x & 31;
   const int gw = blockIdx.x * (kNllThreads / 32) + (threadIdx.x >> 5);
   const int64_t r_lo = min((int64_t)gw * rpw, n), r_hi = min(r_lo + rpw, n);
-  const int C2 = 2 * C;
   const int c0 = 2 * lane;
   const bool has0 = c0 < C, has1 = c0 + 1 < C;
   ff acc0 = ff_zero(), acc1 = ff_zero(), dl0 = ff_zero(), dl1 = ff_zero();
@@ -97,7 +101,7 @@ __global__ void __launch_bounds__(kNllThreads, 2) k_nll_scan(const float* Y, int
       const bool in = r < r_hi;
       v0[u] = 0.f;
       v1[u] = 0.f;
-      if (in) load_pair(Y + r * C2, C, c0, has0, has1, v0[u], v1[u]);
+      if (in) load_pair(eta + r * C, C, c0, has0, has1, v0[u], v1[u]);
       st[u] = in ? status[r] : (int8_t)0;
     }
     float p0 = 0.f, p1 = 0.f, q0 = 0.f, q1 = 0.f;
@@ -237,16 +241,19 @@ __global__ void __launch_bounds__(256) k_nll_lambda(const double* den, const int
 }
 
 // Backward per row: G_ic = g_c (e_ic Lambda_c(group of i) - delta_i), written
-// as bf16 [hi | lo] (row i: 2C values).
-__global__ void __launch_bounds__(kNllThreads, 2) k_nll_grad(const float* Y, int64_t n, int C, const int8_t* status,
-                                                          const int32_t* gend, const int32_t* wk0, int64_t rpw,
-                                                          const float* lam, const double* gout, __nv_bfloat16* Gcat) {
+// as bf16 in the layout of Bcat: row i holds 2 Cp values, hi(G_ic) at c,
+// lo(G_ic) = bf16(G_ic - hi) at Cp + c, zeros in the padding columns.
+__global__ void __launch_bounds__(kNllThreads, 2) k_nll_grad(const float* eta, int64_t n, int C, int Cp,
+                                                          const int8_t* status, const int32_t* gend,
+                                                          const int32_t* wk0, int64_t rpw, const float* lam,
+                                                          const double* gout, __nv_bfloat16* Gcat) {
   const int lane = threadIdx.x & 31;
   const int gw = blockIdx.x * (kNllThreads / 32) + (threadIdx.x >> 5);
   const int64_t r_lo = min((int64_t)gw * rpw, n), r_hi = min(r_lo + rpw, n);
-  const int C2 = 2 * C;
+  const int NB = 2 * Cp;
   const int c0 = 2 * lane;
   const bool has0 = c0 < C, has1 = c0 + 1 < C;
+  const bool pad = c0 < Cp;   // lanes whose column pair lies in [0, Cp): they also write the padding zeros
   const float g0 = has0 ? (float)gout[c0] : 0.f, g1 = has1 ? (float)gout[c0 + 1] : 0.f;
   if (r_lo >= r_hi) return;  // warps past the last row
   int kn = wk0[gw];  // group of the current row: the first end at or after it
@@ -266,7 +273,7 @@ __global__ void __launch_bounds__(kNllThreads, 2) k_nll_grad(const float* Y, int
       const bool in = r < r_hi;
       v0[u] = 0.f;
       v1[u] = 0.f;
-      if (in) load_pair(Y + r * C2, C, c0, has0, has1, v0[u], v1[u]);
+      if (in) load_pair(eta + r * C, C, c0, has0, has1, v0[u], v1[u]);
       st[u] = in ? status[r] : (int8_t)0;
     }
 #pragma unroll
@@ -279,24 +286,15 @@ __global__ void __launch_bounds__(kNllThreads, 2) k_nll_grad(const float* Y, int
         load_lam();
       }
       const float d = st[u] == 1 ? 1.f : 0.f;
-      __nv_bfloat16* g = Gcat + r * C2;
+      __nv_bfloat16* g = Gcat + r * NB;
       const float x0 = has0 ? g0 * (expf(v0[u]) * l0 - d) : 0.f;
       const float x1 = has1 ? g1 * (expf(v1[u]) * l1 - d) : 0.f;
       const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
       const __nv_bfloat16 m0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
       const __nv_bfloat16 m1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
-      if (has1 && (C & 1) == 0) {  // 4-byte stores of both columns
+      if (pad) {  // Cp is a multiple of 16, so c0 + 1 < Cp too: 4-byte stores
         *reinterpret_cast<__nv_bfloat162*>(g + c0) = __halves2bfloat162(h0, h1);
-        *reinterpret_cast<__nv_bfloat162*>(g + C + c0) = __halves2bfloat162(m0, m1);
-      } else {
-        if (has0) {
-          g[c0] = h0;
-          g[C + c0] = m0;
-        }
-        if (has1) {
-          g[c0 + 1] = h1;
-          g[C + c0 + 1] = m1;
-        }
+        *reinterpret_cast<__nv_bfloat162*>(g + Cp + c0) = __halves2bfloat162(m0, m1);
       }
     }
   }
@@ -308,14 +306,6 @@ int cuda_err(cudaError_t e, const char* what) {
   snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
   set_last_error_text(buf);
   return e == cudaErrorMemoryAllocation ? SURV_E_NOMEM : SURV_E_CUDA;
-}
-
-int blas_err(cublasStatus_t e, const char* what) {
-  if (e == CUBLAS_STATUS_SUCCESS) return SURV_OK;
-  char buf[256];
-  snprintf(buf, sizeof(buf), "%s: cuBLAS status %d", what, (int)e);
-  set_last_error_text(buf);
-  return e == CUBLAS_STATUS_ALLOC_FAILED ? SURV_E_NOMEM : SURV_E_CUDA;
 }
 
 // Device memory of the current device, or managed memory.
@@ -335,17 +325,6 @@ bool on_device(const void* p) {
   return a.type == cudaMemoryTypeDevice && a.device == cur;
 }
 
-int get_blas(surv_workspace* ws, cudaStream_t s, cublasHandle_t* h) {
-  if (!ws->blas) {
-    cublasHandle_t nh = nullptr;
-    int rc = blas_err(cublasCreate(&nh), "cublasCreate");
-    if (rc) return rc;
-    ws->blas = nh;
-  }
-  *h = static_cast<cublasHandle_t>(ws->blas);
-  return blas_err(cublasSetStream(*h, s), "cublasSetStream");
-}
-
 struct NllCtrl {
   unsigned perr;
   int32_t K;
@@ -360,13 +339,6 @@ struct NllCtrl {
   } while (0)
 
 }  // namespace
-
-void ws_release_blas(surv_workspace* ws) {
-  if (ws && ws->blas) {
-    cublasDestroy(static_cast<cublasHandle_t>(ws->blas));
-    ws->blas = nullptr;
-  }
-}
 
 }  // namespace survgpu
 
@@ -388,6 +360,10 @@ int cox_nll_forward(const surv_nll_data* d, const float* B, double* nll, void* s
     set_last_error_text("time, status, X, B and nll must be device memory");
     return SURV_E_INVALID;
   }
+  if (n > 0x7fffff00 || !nll_tc_fits((int)std::min<int64_t>(p, 1 << 20), C)) {
+    set_last_error_text("p too large: X B keeps B in shared memory (p <= 512 for 64 columns)");
+    return SURV_E_INVALID;
+  }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   using W = surv_workspace;
   void *ctrl_v, *blk, *gend, *dk, *ck, *wk0, *Y, *Bcat, *rec, *wt, *den;
@@ -401,8 +377,19 @@ int cox_nll_forward(const surv_nll_data* d, const float* B, double* nll, void* s
   NLL_TRY(ws_ensure(ws, W::NLL_BLK, 4 * (size_t)nb, &blk));
   NLL_TRY(cuda_err(prep_count_ends(time, n, static_cast<int32_t*>(blk), &ctrl->K, s), "count ends"));
   NllCtrl hc;
+  unsigned prev_err = 0;
   NLL_TRY(cuda_err(cudaMemcpyAsync(&hc, ctrl, sizeof(hc), cudaMemcpyDeviceToHost, s), "copy"));
+  if (ws->nll_err_init)
+    NLL_TRY(cuda_err(cudaMemcpyAsync(&prev_err, ws->bufs[W::NLL_ERR].p, sizeof(unsigned), cudaMemcpyDeviceToHost, s),
+                     "copy"));
   NLL_TRY(cuda_err(cudaStreamSynchronize(s), "sync"));
+  if (prev_err) {
+    // a bounded wait of an earlier forward or backward on this workspace
+    // expired: its results were not valid
+    NLL_TRY(cuda_err(cudaMemsetAsync(ws->bufs[W::NLL_ERR].p, 0, sizeof(unsigned), s), "memset"));
+    set_last_error_text("a device-side wait of an earlier cox_nll call on this workspace expired");
+    return SURV_E_DEVICE_TIMEOUT;
+  }
   if (hc.perr & PREP_UNSORTED) { set_last_error_text("time is not non-increasing"); return SURV_E_UNSORTED; }
   if (hc.perr & PREP_STATUS) { set_last_error_text("status code out of range"); return SURV_E_STATUS; }
   const int K = hc.K;
@@ -425,20 +412,34 @@ int cox_nll_forward(const surv_nll_data* d, const float* B, double* nll, void* s
   NLL_TRY(ws_ensure(ws, W::NLL_WK0, 4 * (size_t)(nwarps + 1), &wk0));
   NLL_TRY(cuda_err(prep_warp_groups(static_cast<int32_t*>(gend), K, n, nwarps, rpw, static_cast<int32_t*>(wk0), s),
                    "warp groups"));
-  // Y = X [B_hi | B_lo]
-  NLL_TRY(ws_ensure(ws, W::NLL_Y, sizeof(float) * (size_t)n * 2 * C, &Y));
-  NLL_TRY(ws_ensure(ws, W::NLL_BCAT, sizeof(__nv_bfloat16) * (size_t)p * 2 * C, &Bcat));
-  const int64_t pc = p * C;
-  k_split_b<<<(unsigned)((pc + 255) / 256), 256, 0, s>>>(B, p, C, static_cast<__nv_bfloat16*>(Bcat));
+  // eta = X B_hi + X B_lo on the tensor cores (nll_tc.cu).  Bcat^T holds the
+  // split in 2 Cp rows, Cp = C rounded up to 16 (at least 32); X and Bcat^T
+  // rows have a pitch of ld = p rounded up to 8 elements (16 bytes)
+  const int Cp = std::max(32, (C + 15) / 16 * 16);
+  const int64_t ld = (p + 7) / 8 * 8;
+  const void* Xt = d->X;
+  if (ld != p || ((uintptr_t)d->X & 15) != 0) {
+    void* xp = nullptr;
+    NLL_TRY(ws_ensure(ws, W::NLL_XP, sizeof(__nv_bfloat16) * (size_t)n * ld, &xp));
+    const int64_t tot = n * ld;
+    k_pad_x<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(static_cast<const __nv_bfloat16*>(d->X), n, p, ld,
+                                                        static_cast<__nv_bfloat16*>(xp));
+    NLL_TRY(cuda_err(cudaGetLastError(), "pad X"));
+    Xt = xp;
+  }
+  NLL_TRY(ws_ensure(ws, W::NLL_Y, sizeof(float) * (size_t)n * C, &Y));
+  NLL_TRY(ws_ensure(ws, W::NLL_BCAT, sizeof(__nv_bfloat16) * (size_t)2 * Cp * ld, &Bcat));
+  void* errw = nullptr;
+  NLL_TRY(ws_ensure(ws, W::NLL_ERR, sizeof(unsigned), &errw));
+  if (!ws->nll_err_init) {
+    NLL_TRY(cuda_err(cudaMemsetAsync(errw, 0, sizeof(unsigned), s), "memset"));
+    ws->nll_err_init = true;
+  }
+  const int64_t nbt = (int64_t)2 * Cp * ld;
+  k_split_bt<<<(unsigned)((nbt + 255) / 256), 256, 0, s>>>(B, p, C, Cp, ld, static_cast<__nv_bfloat16*>(Bcat));
   NLL_TRY(cuda_err(cudaGetLastError(), "split B"));
-  cublasHandle_t h;
-  NLL_TRY(get_blas(ws, s, &h));
-  const float one = 1.f, zero = 0.f;
-  // column-major view: Y^T (2C x n) = Bcat^T (2C x p) * X^T (p x n)
-  NLL_TRY(blas_err(cublasGemmEx(h, CUBLAS_OP_N, CUBLAS_OP_N, 2 * C, (int)n, (int)p, &one, Bcat, CUDA_R_16BF, 2 * C,
-                                d->X, CUDA_R_16BF, (int)p, &zero, Y, CUDA_R_32F, 2 * C, CUBLAS_COMPUTE_32F,
-                                CUBLAS_GEMM_DEFAULT),
-                   "GEMM X B"));
+  NLL_TRY(cuda_err(nll_xb_tc(Xt, n, (int)p, ld, Bcat, C, Cp, static_cast<float*>(Y), static_cast<unsigned*>(errw), s),
+                   "tensor-core X B"));
   NLL_TRY(ws_ensure(ws, W::NLL_REC, sizeof(float2) * (size_t)K * C, &rec));
   NLL_TRY(ws_ensure(ws, W::NLL_WT, 2 * sizeof(float2) * (size_t)nwarps * C, &wt));
   NLL_TRY(ws_ensure(ws, W::NLL_DEN, sizeof(double) * (size_t)K * C, &den));
@@ -463,6 +464,8 @@ int cox_nll_forward(const surv_nll_data* d, const float* B, double* nll, void* s
   ws->nll_wpc = wpc;
   ws->nll_wpw = (int32_t)wpw;
   ws->nll_x = d->X;
+  ws->nll_xt = Xt;
+  ws->nll_ld = ld;
   return SURV_OK;
 }
 
@@ -484,33 +487,30 @@ int cox_nll_backward(const surv_nll_data* d, const double* grad_nll, float* grad
   const int64_t n = d->n, p = d->p;
   const int C = d->ncols, K = ws->nll_K, G = ws->nll_G, nwarps = G * ws->nll_wpc;
   const int64_t rpw = (int64_t)ws->nll_wpw * 32;
-  void *lam, *G2, *gB;
+  void *lam, *G2, *part;
+  const int Cp = std::max(32, (C + 15) / 16 * 16);
+  const int NB = 2 * Cp;
+  int nx = 0;
+  const size_t part_floats = nll_xtg_part_floats(n, (int)p, NB, &nx);
   NLL_TRY(ws_ensure(ws, W::NLL_LAM, sizeof(float) * (size_t)K * C, &lam));
-  NLL_TRY(ws_ensure(ws, W::NLL_G, sizeof(__nv_bfloat16) * (size_t)n * 2 * C, &G2));
-  NLL_TRY(ws_ensure(ws, W::NLL_GB, sizeof(float) * (size_t)p * 2 * C, &gB));
+  NLL_TRY(ws_ensure(ws, W::NLL_G, sizeof(__nv_bfloat16) * (size_t)n * NB, &G2));
+  NLL_TRY(ws_ensure(ws, W::NLL_GB, sizeof(float) * part_floats, &part));
   const double* den = static_cast<const double*>(ws->bufs[W::NLL_DEN].p);
   const int32_t* dk = static_cast<const int32_t*>(ws->bufs[W::NLL_DK].p);
   const int32_t* gend = static_cast<const int32_t*>(ws->bufs[W::NLL_GEND].p);
   const int32_t* wk0 = static_cast<const int32_t*>(ws->bufs[W::NLL_WK0].p);
   k_nll_lambda<<<C, 256, 0, s>>>(den, dk, K, C, static_cast<float*>(lam));
   NLL_TRY(cuda_err(cudaGetLastError(), "lambda"));
-  k_nll_grad<<<G, kNllThreads, 0, s>>>(static_cast<const float*>(ws->bufs[W::NLL_Y].p), n, C,
+  k_nll_grad<<<G, kNllThreads, 0, s>>>(static_cast<const float*>(ws->bufs[W::NLL_Y].p), n, C, Cp,
                                        static_cast<const int8_t*>(d->status), gend, wk0, rpw,
                                        static_cast<float*>(lam), grad_nll, static_cast<__nv_bfloat16*>(G2));
   NLL_TRY(cuda_err(cudaGetLastError(), "grad"));
   (void)nwarps;
-  cublasHandle_t h;
-  NLL_TRY(get_blas(ws, s, &h));
-  const float one = 1.f, zero = 0.f;
-  // column-major: gBcat (p x 2C) = X^T (p x n) * Gcat (n x 2C); Gcat is stored
-  // row-major n x 2C, i.e. column-major (2C x n), hence the transpose
-  NLL_TRY(blas_err(cublasGemmEx(h, CUBLAS_OP_N, CUBLAS_OP_T, (int)p, 2 * C, (int)n, &one, d->X, CUDA_R_16BF, (int)p,
-                                G2, CUDA_R_16BF, 2 * C, &zero, gB, CUDA_R_32F, (int)p, CUBLAS_COMPUTE_32F,
-                                CUBLAS_GEMM_DEFAULT),
-                   "GEMM X^T G"));
-  const int64_t pc = p * C;
-  k_sum_halves<<<(unsigned)((pc + 255) / 256), 256, 0, s>>>(static_cast<const float*>(gB), p, C, grad_B);
-  return cuda_err(cudaGetLastError(), "sum halves");
+  // grad_B = X^T [G_hi | G_lo] on the tensor cores, halves and CTA partials
+  // summed in FP64 (nll_tc.cu)
+  return cuda_err(nll_xtg_tc(ws->nll_xt, n, (int)p, ws->nll_ld, G2, C, Cp, static_cast<float*>(part), nx, grad_B,
+                             static_cast<unsigned*>(ws->bufs[W::NLL_ERR].p), s),
+                  "tensor-core X^T G");
 }
 
 }  // extern "C"

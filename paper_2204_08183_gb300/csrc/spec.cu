@@ -485,12 +485,12 @@ __global__ void __launch_bounds__(kStNT) k_strans(const __grid_constant__ CcdPar
 //             of e, so one DRAM and one L2 round trip serve all B columns;
 //             the lanes keep float-float partials and one reduce-scatter
 //             over the R components gives the warp totals.
-//   k_itrans  one CTA per kItF pass CTAs: the prefix of the pass CTAs'
-//             aggregates before its range, G_k of the B columns at its group
-//             ends, partial sums; the last CTA commits the batch.  It reads
-//             its control line before waiting: the line was written by the
-//             previous batch's transform, which finished before this batch's
-//             pass kernel passed its own wait.
+//   k_itrans  every CTA scans the pass CTAs' aggregates (one per thread, in
+//             shared memory) and takes an even share of the (group end,
+//             column) items: G_k of the B columns, partial sums; the last CTA
+//             commits the batch.  It reads its control line before waiting:
+//             the line was written by the previous batch's transform, which
+//             finished before this batch's pass kernel passed its own wait.
 template <int B>
 struct IpCfg {
   static constexpr int R = 1 + B;
@@ -499,7 +499,6 @@ struct IpCfg {
   static constexpr int NPP = NP <= 2 ? 2 : (NP <= 4 ? 4 : (NP <= 8 ? 8 : (NP <= 16 ? 16 : 32)));
   static constexpr int SR = B <= 4 ? 2 : 1;  // rounds of 32 nonzeros per column in flight
 };
-constexpr int kItF = 8;      // pass CTAs per transform CTA
 constexpr int kItNT = 512;   // transform kernel threads
 constexpr int kItWarps = kItNT / 32;
 
@@ -652,18 +651,16 @@ __global__ void __launch_bounds__(kSpNT, 2) k_ipass(const __grid_constant__ CcdP
 
 template <int B>
 __global__ void __launch_bounds__(kItNT) k_itrans(const __grid_constant__ CcdParams P, int slot) {
-  constexpr int R = IpCfg<B>::R, RP = IpCfg<B>::RP, NP = IpCfg<B>::NP, NPP = IpCfg<B>::NPP;
-  constexpr int NR = NP > R ? NP : R;
-  __shared__ ff s_red[kItWarps][NR];
-  __shared__ ff s_T[kItF][R];
+  constexpr int R = IpCfg<B>::R, NP = IpCfg<B>::NP, NPP = IpCfg<B>::NPP;
+  __shared__ ff s_T[kItNT][R];           // exclusive prefix of the pass CTAs' aggregates (G <= kItNT)
+  __shared__ ff s_w[kItWarps][R];        // warp totals of that scan, then their exclusive prefix
+  __shared__ ff s_red[kItWarps][NP];
   __shared__ ff s_tot[NP];
   __shared__ int s_stop, s_j0, s_last;
   __shared__ double s_lin[2];
   GraphCtl* ctl = P.gctl;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int WPC = P.wpc, G = P.G, G2 = gridDim.x, c2 = blockIdx.x;
-  const int q_lo = c2 * kItF, q_hi = min(q_lo + kItF, G);
-  const int kc_lo = P.wk0[q_lo * WPC], kc_hi = P.wk0[q_hi * WPC];
   LineView lv;
   long long batches_prev = 0;
   if (tid == 0) {
@@ -680,47 +677,58 @@ __global__ void __launch_bounds__(kItNT) k_itrans(const __grid_constant__ CcdPar
   const int j0 = s_j0;
   const int nb = min(B, P.p - j0);
   const bool eval = j0 == 0;
-  const int nwork = (kc_hi - kc_lo) * nb;
-  // the first work item's group table entries (written by the prep)
-  int k1 = 0, b1 = 0, d1 = 0, gw1 = 0;
-  if (tid < nwork) {
-    k1 = kc_lo + tid / nb;
-    b1 = tid - (tid / nb) * nb;
-    d1 = P.dk[k1];
-    gw1 = (int)((P.gend[k1] >> 5) / P.wpw);
+  // work items (group end k, column b), k = item / nb, spread over all
+  // threads of the grid; the first item's group table entries (written by
+  // the prep) are loaded before the wait
+  const int nwork = P.K * nb;
+  const int stride = G2 * kItNT;
+  const int it0 = c2 * kItNT + tid;
+  int d1 = 0, gw1 = 0;
+  if (it0 < nwork) {
+    const int k = it0 / nb;
+    d1 = P.dk[k];
+    gw1 = (int)((P.gend[k] >> 5) / P.wpw);
   }
   pdl_wait();
 
-  // prefix of the pass CTAs' aggregates before q_lo, then within the range
+  // exclusive prefix over the pass CTAs of their aggregates, fixed order
   {
-    ff t[RP];
+    ff v[R];
 #pragma unroll
-    for (int m = 0; m < RP; ++m) t[m] = ff_zero();
-    for (int q = tid; q < q_lo; q += kItNT)
+    for (int m = 0; m < R; ++m) v[m] = tid < G ? unpack8<ff>(__ldcg(P.agg + (size_t)m * G + tid)) : ff_zero();
+    ff incl[R];
 #pragma unroll
-      for (int m = 0; m < R; ++m) t[m] = ff_add(t[m], unpack8<ff>(__ldcg(P.agg + (size_t)m * G + q)));
-    warp_reduce_scatter<RP>(t, lane);
-    const int comp = warp_rs_component<RP>(lane);
-    if (comp < R && lane == warp_rs_lane<RP>(comp)) s_red[w][comp] = t[0];
-  }
-  __syncthreads();
-  if (tid < R) {
-    uint64_t ag[kItF];
+    for (int m = 0; m < R; ++m) incl[m] = v[m];
+    warp_scan_n<R>(incl, lane);
 #pragma unroll
-    for (int f = 0; f < kItF; ++f) ag[f] = q_lo + f < q_hi ? __ldcg(P.agg + (size_t)tid * G + q_lo + f) : 0ull;
-    ff a = s_red[0][tid];
-    for (int q = 1; q < kItWarps; ++q) a = ff_add(a, s_red[q][tid]);
-#pragma unroll
-    for (int f = 0; f < kItF; ++f) {
-      s_T[f][tid] = a;
-      a = ff_add(a, unpack8<ff>(ag[f]));
+    for (int m = 0; m < R; ++m) {
+      ff ex = shfl_up(incl[m], 1);
+      v[m] = lane == 0 ? ff_zero() : ex;   // exclusive within the warp
     }
+    if (lane == 31)
+#pragma unroll
+      for (int m = 0; m < R; ++m) s_w[w][m] = incl[m];
+    __syncthreads();
+    if (w == 0) {
+      ff t[R];
+#pragma unroll
+      for (int m = 0; m < R; ++m) t[m] = lane < kItWarps ? s_w[lane][m] : ff_zero();
+      warp_scan_n<R>(t, lane);
+      __syncwarp();
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        const ff ex = shfl_up(t[m], 1);
+        if (lane < kItWarps) s_w[lane][m] = lane == 0 ? ff_zero() : ex;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < R; ++m) s_T[tid][m] = ff_add(s_w[w][m], v[m]);
   }
   __syncthreads();
 
-  // G_k of the batch's columns at the range's group ends (steps 3-4): one
-  // thread per (group end, column); column 0's thread also adds d_k log
-  // den_k on evaluation passes
+  // G_k of the batch's columns at the group ends (steps 3-4); column 0's
+  // item also adds d_k log den_k on evaluation passes
   ff f1[B], f2[B];
 #pragma unroll
   for (int b = 0; b < B; ++b) {
@@ -729,18 +737,17 @@ __global__ void __launch_bounds__(kItNT) k_itrans(const __grid_constant__ CcdPar
   }
   double pl = 0.0;
   const ff* rec = reinterpret_cast<const ff*>(P.rec);
-  for (int it = tid; it < nwork; it += kItNT) {
-    int k, b, d, gwk;
-    if (it == tid) {
-      k = k1, b = b1, d = d1, gwk = gw1;
+  for (int it = it0; it < nwork; it += stride) {
+    const int k = it / nb, b = it - k * nb;
+    int d, gwk;
+    if (it == it0) {
+      d = d1, gwk = gw1;
     } else {
-      k = kc_lo + it / nb;
-      b = it - (it / nb) * nb;
       d = P.dk[k];
       gwk = (int)((P.gend[k] >> 5) / P.wpw);
     }
     if (d == 0) continue;
-    const int f = gwk / WPC - q_lo;
+    const int f = gwk / WPC;
     const ff den = ff_add(ff_add(s_T[f][0], unpack8<ff>(__ldcg(P.wt + gwk))), rec[(size_t)k * R]);
     const ff n1 = ff_add(ff_add(s_T[f][1 + b], unpack8<ff>(__ldcg(P.wt + (size_t)(1 + b) * P.nwarps + gwk))),
                          rec[(size_t)k * R + 1 + b]);
@@ -809,6 +816,10 @@ __global__ void __launch_bounds__(kItNT) k_itrans(const __grid_constant__ CcdPar
   commit_batch<B>(P, lv, batches_prev, j0, nb, eval, s_tot, s_lin);
 }
 
+// CTAs of the transform kernel for K group ends and B columns: about one
+// (end, column) item per thread, at least 8, at most 152.
+int itrans_ctas(int K, int B) { return std::max(8, std::min(152, (K * B + kItNT - 1) / kItNT)); }
+
 template <int B>
 cudaError_t capture_spec(const CcdParams& P, int S, bool pdl, cudaStream_t cs, cudaGraph_t* g) {
   cudaError_t st = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
@@ -827,7 +838,8 @@ cudaError_t capture_spec(const CcdParams& P, int S, bool pdl, cudaStream_t cs, c
   // indicator columns: the lockstep walks and the ranged transform
   const bool ind = P.values == nullptr;
   if (ind) {
-    ct.gridDim = dim3((P.G + kItF - 1) / kItF);
+    if (P.G > kItNT) return cudaErrorInvalidValue;   // the transform scans one aggregate per thread
+    ct.gridDim = dim3(itrans_ctas(P.K, B));
     ct.blockDim = dim3(kItNT);
   }
   cudaError_t lst = cudaSuccess;

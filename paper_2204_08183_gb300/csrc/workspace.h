@@ -19,7 +19,7 @@ struct surv_workspace {
     SLOTS, CTRL, BLOCKCNT, SORTWORK, PERM, PF, WT, AGG,
     // differentiable form (cox_nll_forward / cox_nll_backward)
     NLL_Y, NLL_BCAT, NLL_REC, NLL_WT, NLL_DEN, NLL_LAM, NLL_G, NLL_GB, NLL_GEND, NLL_DK, NLL_WK0, NLL_BLK,
-    NLL_CTRL,
+    NLL_CTRL, NLL_XP, NLL_ERR,
     // cross-validated path (cox_cv_path) and lambda_max
     CV_FOLD, CV_DK, CV_DTX, CV_E, CV_ETA, CV_REC, CV_WT, CV_AGG, CV_PART, CV_GCTL, CV_BETA, CV_WIDTH, CV_PEN,
     CV_OUT, CV_FITS, CV_CTRL, CV_DEN, CV_HELD, CV_MEAN, LM_LAM, LM_R, LM_G,
@@ -30,11 +30,13 @@ struct surv_workspace {
   int device = -1;
   Buf bufs[NBUF];
   survgpu::GraphCache graph;  // instantiated sweep graph of the last fit
-  void* blas = nullptr;       // cublasHandle_t, created on first use
   // shape of the last cox_nll_forward (what cox_nll_backward continues from)
   int64_t nll_n = -1;
   int32_t nll_p = 0, nll_c = 0, nll_K = 0, nll_G = 0, nll_wpc = 0, nll_wpw = 0;
   const void* nll_x = nullptr;
+  const void* nll_xt = nullptr;   // X as the tensor-core kernels read it (padded copy if needed)
+  int64_t nll_ld = 0;              // its row pitch in elements
+  bool nll_err_init = false;       // the tensor-core kernels' error word has been zeroed
   // CTAs per fit chosen by the cross-validation tuner, and the shape it was
   // tuned for (n, p, fits, layout * 2 + precision, dtype, layout tag)
   int32_t cv_tuned_ctas = 0;
@@ -44,6 +46,16 @@ struct surv_workspace {
 namespace survgpu {
 // Grow buffer `id` to at least `bytes` (api.cu); SURV_* error code.
 int ws_ensure(surv_workspace* ws, int id, size_t bytes, void** out);
-// Destroy the cuBLAS handle of a workspace, if any (nll.cu).
-void ws_release_blas(surv_workspace* ws);
+// Tensor-core products of the differentiable form (nll_tc.cu).  X: n rows of
+// p bfloat16 with row pitch ldx (a multiple of 8, 16-byte aligned base);
+// BcatT / Gcat: the bf16 split in 2 Cp columns (hi at c, lo at Cp + c).  A
+// bounded device wait that expires sets *err.
+cudaError_t nll_xb_tc(const void* X, int64_t n, int p, int64_t ldx, const void* BcatT, int C, int Cp, float* eta,
+                      unsigned* err, cudaStream_t s);
+size_t nll_xtg_part_floats(int64_t n, int p, int NB, int* nx);
+// Whether X B with p covariates and C columns fits the forward kernel (B is
+// kept in shared memory beside at least three X stages).
+bool nll_tc_fits(int p, int C);
+cudaError_t nll_xtg_tc(const void* X, int64_t n, int p, int64_t ldx, const void* Gcat, int C, int Cp, float* part,
+                       int nx, float* grad_B, unsigned* err, cudaStream_t s);
 }  // namespace survgpu
