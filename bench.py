@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--cv-p", type=int, default=500, help="cv: covariates (500 = the benchmarked size; smaller "
                                                            "values give small cases for profiling)")
     ap.add_argument("--no-sequential", action="store_true", help="cv: skip the 200 sequential plain fits")
+    ap.add_argument("--spec-b", type=int, choices=[4, 8], default=4,
+                    help="coordinates per speculative batch of the default schedule (8: SURV_FLAG_SPEC_B8)")
     ap.add_argument("--schedule", choices=["graph", "one", "persistent"], default="graph",
                     help="graph: the default schedule (two kernels per row pass replayed as a CUDA graph, "
                          "speculative batches of 4 coordinates per row pass); one: one coordinate per row "
@@ -180,6 +182,8 @@ def run_gpu(args, rank, world):
         flags = binding.SURV_FLAG_SPARSE_NUMERATOR
     if args.schedule == "one":
         flags = binding.SURV_FLAG_ONE_COORDINATE
+    if args.spec_b == 8 and not sn and args.schedule == "graph":
+        flags |= binding.SURV_FLAG_SPEC_B8
     kw = dict(penalty="l1", lam=lam, tol=1e-8, max_sweeps=1000, workspace=ws, flags=flags)
     beta_dev = torch.zeros(p, dtype=torch.float64, device="cuda")
     # the sampler starts before the warm-up so that its start-up cannot fall
@@ -242,7 +246,7 @@ def run_gpu(args, rank, world):
     if batched:
         # speculative batches: a row pass reads e once and the slices of up
         # to 4 columns (counted as 4: an upper bound on the columns read)
-        per_row_pass = 4 * n + 4 * (4 + vb) * nnz / p + 8 * K
+        per_row_pass = 4 * n + args.spec_b * (4 + vb) * nnz / p + 8 * K
         alg_bytes = row_passes * per_row_pass + upd * per_update
     if sn:
         # per coordinate: column j (row, value) and, per nonzero, e, its
@@ -269,9 +273,10 @@ def run_gpu(args, rank, world):
                 "us_per_coordinate": round(us_per_coord, 3),
                 "passes_per_fit": passes / len(infos), "eta_updates_per_fit": upd / len(infos),
                 "row_passes_per_fit": row_passes / len(infos)}
+    bw4 = args.spec_b == 4
     if batched:
-        roofline["unit_of_work"] = "one row pass (a speculative batch of up to 4 coordinates)"
-        if n == 10_000_000 and p == 100 and ind and TRAFFIC_IND_ROW_PASS:
+        roofline["unit_of_work"] = "one row pass (a speculative batch of up to %d coordinates)" % args.spec_b
+        if n == 10_000_000 and p == 100 and ind and bw4 and TRAFFIC_IND_ROW_PASS:
             # dram__bytes_read.sum + dram__bytes_write.sum of k_ipass<4> +
             # k_itrans<4> per row pass, steady state (ncu --cache-control
             # none); see profiles/k_ipass_k_itrans_cox_csc_n1e7.md
@@ -293,8 +298,9 @@ def run_gpu(args, rank, world):
     roofline["kernel"] = ("ccd_kernel<cox,csc,f32> (persistent, one launch per fit)" if args.schedule == "persistent"
                           else "k_pass + k_trans <cox,csc,f32>, one pair per coordinate, one graph replay per sweep")
     if batched:
-        roofline["kernel"] = (("k_ipass<4> + k_itrans<4>" if ind else "k_spass<4> + k_strans<4>") +
-                              ": one pair per speculative batch of 4 coordinates, graph replays of batches")
+        bw = args.spec_b
+        roofline["kernel"] = (("k_ipass<%d> + k_itrans<%d>" if ind else "k_spass<%d> + k_strans<%d>") % (bw, bw) +
+                              ": one pair per speculative batch of %d coordinates, graph replays of batches" % bw)
     if sn:
         roofline["kernel"] = ("k_sn_den_a/den_b/lam (after nonzero steps only) + k_sn_col_a/col_b per coordinate, "
                               "one graph replay per sweep")

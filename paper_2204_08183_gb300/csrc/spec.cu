@@ -244,6 +244,25 @@ __global__ void __launch_bounds__(kSpNT, 2) k_spass(const __grid_constant__ CcdP
   }
 }
 
+// CoordIn: lane b's beta, trust-region width, lambda * penalty factor and
+// delta^T X of coordinate j0 + b (loaded by the caller, possibly early).
+struct CoordIn {
+  double beta = 0.0, width = 0.0, pen = 0.0, dtx = 0.0;
+};
+__device__ __forceinline__ CoordIn load_coord(const CcdParams& P, int j0, int nb) {
+  const int lane = threadIdx.x & 31;
+  CoordIn c;
+  if (lane < nb) {
+    const int j = j0 + lane;
+    c.beta = __ldcg(P.beta + j);
+    c.width = __ldcg(P.width + j);
+    c.pen = P.pen[j];
+    c.dtx = P.dTx[j];
+  }
+  return c;
+}
+
+
 // Warp 0 of a batch's last transform CTA: on j0 = 0 the objective at the
 // start of the sweep and the stopping rule; then lane b takes the candidate
 // step of coordinate j0 + b (Section 2.4) from the batch's sums s_tot
@@ -252,7 +271,8 @@ __global__ void __launch_bounds__(kSpNT, 2) k_spass(const __grid_constant__ CcdP
 // every lane writes one replica of the control line for the next batch.
 template <int B>
 __device__ __forceinline__ void commit_batch(const CcdParams& P, const LineView& lv, long long batches_prev, int j0,
-                                             int nb, bool eval, const ff* s_tot, const double* s_lin) {
+                                             int nb, bool eval, const ff* s_tot, const double* s_lin,
+                                             const CoordIn& ci) {
   GraphCtl* ctl = P.gctl;
   const int lane = threadIdx.x & 31;
   // objective at the start of the sweep and the stopping rule (j0 = 0)
@@ -288,10 +308,10 @@ __device__ __forceinline__ void commit_batch(const CcdParams& P, const LineView&
   double applied = 0.0, bnew = 0.0, wnew = 0.0;
   const int j = j0 + lane;
   if (!stop && lane < nb) {
-    const double beta = __ldcg(P.beta + j), width = __ldcg(P.width + j);
-    const double grad = P.dTx[j] - ff_to_d(s_tot[lane]);  // l' = delta^T X_j - sum_k d_k G_k
+    const double beta = ci.beta, width = ci.width;
+    const double grad = ci.dtx - ff_to_d(s_tot[lane]);    // l' = delta^T X_j - sum_k d_k G_k
     const double hess = -ff_to_d(s_tot[B + lane]);         // l''
-    const double step = newton_step(beta, grad, hess, P.penalty, P.pen[j]);
+    const double step = newton_step(beta, grad, hess, P.penalty, ci.pen);
     if (step != 0.0) applied = copysign(fmin(fabs(step), width), step);
     bnew = beta + applied;
     wnew = fmax(2.0 * fabs(applied), width / 2.0);
@@ -472,7 +492,7 @@ __global__ void __launch_bounds__(kStNT) k_strans(const __grid_constant__ CcdPar
   }
   __syncthreads();
   if (w != 0) return;
-  commit_batch<B>(P, lv, batches_prev, j0, nb, eval, s_tot, s_lin);
+  commit_batch<B>(P, lv, batches_prev, j0, nb, eval, s_tot, s_lin, load_coord(P, j0, nb));
 }
 
 
@@ -515,10 +535,26 @@ __device__ __forceinline__ int end_at(const int32_t* gend, int k, int k_lo, int 
 // len[b] entries.  At each group end before a column's last nonzero the
 // warp-relative prefix of e x is stored in rec[k * R + 1 + b]; acc[b] gets
 // the lane partials, kn[b] the first end not written.
+// The row indices of the first 32 SR nonzeros of each column are loaded by
+// ip_first_rows before the dense walk, so their DRAM latency overlaps it.
+template <int B, int SR>
+__device__ __forceinline__ void ip_first_rows(const int32_t* const (&col)[B], const int (&len)[B],
+                                              int (&row0)[B][SR]) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t strm = l2_stream();
+#pragma unroll
+  for (int b = 0; b < B; ++b)
+#pragma unroll
+    for (int r = 0; r < SR; ++r) {
+      const int i = 32 * r + lane;
+      row0[b][r] = i < len[b] ? ld_hint(col[b] + i, strm) : INT_MAX;
+    }
+}
+
 template <int B, int SR>
 __device__ __forceinline__ void ip_sparse(const float* e, const int32_t* gend, const int32_t* const (&col)[B],
                                           const int (&len)[B], ff* rec, int R, int k_lo, int k_hi, int kreg,
-                                          ff (&acc)[B], int (&kn)[B]) {
+                                          const int (&row0)[B][SR], ff (&acc)[B], int (&kn)[B]) {
   const int lane = threadIdx.x & 31;
   const uint64_t keep = l2_keep(), strm = l2_stream();
   int ne[B];
@@ -538,7 +574,7 @@ __device__ __forceinline__ void ip_sparse(const float* e, const int32_t* gend, c
 #pragma unroll
       for (int r = 0; r < SR; ++r) {
         const int i = base + 32 * r + lane;
-        row[b][r] = i < len[b] ? ld_hint(col[b] + i, strm) : INT_MAX;
+        row[b][r] = base == 0 ? row0[b][r] : (i < len[b] ? ld_hint(col[b] + i, strm) : INT_MAX);
       }
 #pragma unroll
     for (int b = 0; b < B; ++b)
@@ -553,9 +589,17 @@ __device__ __forceinline__ void ip_sparse(const float* e, const int32_t* gend, c
         const int nvalid = min(32, len[b] - rb);
         const int last_row = __shfl_sync(0xffffffffu, row[b][r], nvalid - 1);
         while (ne[b] < last_row) {
-          ff pref = ff_add_f(acc[b], row[b][r] <= ne[b] ? ev[b][r] : 0.f);
-          pref = warp_sum(pref);
-          if (lane == 0) rec[(size_t)kn[b] * R + 1 + b] = pref;
+          // the warp-relative prefix at the end: the lanes' float-float
+          // partials summed as two FP32 trees (high and low words), error at
+          // most 5u of this warp's piece of the prefix
+          const ff v = ff_add_f(acc[b], row[b][r] <= ne[b] ? ev[b][r] : 0.f);
+          float h = v.hi, l = v.lo;
+#pragma unroll
+          for (int d = 16; d > 0; d >>= 1) {
+            h += __shfl_xor_sync(0xffffffffu, h, d);
+            l += __shfl_xor_sync(0xffffffffu, l, d);
+          }
+          if (lane == 0) rec[(size_t)kn[b] * R + 1 + b] = fast_two_sum(h, l);
           ++kn[b];
           ne[b] = end_at(gend, kn[b], k_lo, k_hi, kreg);
         }
@@ -609,12 +653,14 @@ __global__ void __launch_bounds__(kSpNT, 2) k_ipass(const __grid_constant__ CcdP
   if (s_applied != 0.0) warp_update<0, float>(P, s_q, gw, row_lo, row_hi, s_applied, ff{s_delta[0], s_delta[1]});
   ff* rec = reinterpret_cast<ff*>(P.rec);
   const float* e = reinterpret_cast<const float*>(P.e);
+  int row0[B][SR];
+  ip_first_rows<B, SR>(col, len, row0);
   ff tot[RP];
   tot[0] = sp_dense(e, P.gend, row_lo, row_hi, rec, R, EndCursor{k_lo, k_hi, k_lo, kreg});
   int kn[B];
   {
     ff acc[B];
-    ip_sparse<B, SR>(e, P.gend, col, len, rec, R, k_lo, k_hi, kreg, acc, kn);
+    ip_sparse<B, SR>(e, P.gend, col, len, rec, R, k_lo, k_hi, kreg, row0, acc, kn);
 #pragma unroll
     for (int b = 0; b < B; ++b) tot[1 + b] = acc[b];
   }
@@ -689,6 +735,10 @@ __global__ void __launch_bounds__(kItNT) k_itrans(const __grid_constant__ CcdPar
     d1 = P.dk[k];
     gw1 = (int)((P.gend[k] >> 5) / P.wpw);
   }
+  // the batch's coordinate scalars for the commit (written by the previous
+  // batch's commit, finished before this kernel launched)
+  CoordIn ci;
+  if (w == 0) ci = load_coord(P, j0, nb);
   pdl_wait();
 
   // exclusive prefix over the pass CTAs of their aggregates, fixed order
@@ -813,7 +863,7 @@ __global__ void __launch_bounds__(kItNT) k_itrans(const __grid_constant__ CcdPar
   }
   __syncthreads();
   if (w != 0) return;
-  commit_batch<B>(P, lv, batches_prev, j0, nb, eval, s_tot, s_lin);
+  commit_batch<B>(P, lv, batches_prev, j0, nb, eval, s_tot, s_lin, ci);
 }
 
 // CTAs of the transform kernel for K group ends and B columns: about one
