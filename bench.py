@@ -52,6 +52,9 @@ def parse():
                     help="subjects (default: the workload's size, 1e7 for ccd/sn, 5e6 for fg)")
     ap.add_argument("--p", type=int, default=None, help="covariates (default: 100 for ccd/sn, 50 for fg)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="headline run only: skip the cross-validated path, Fine-Gray and autograd lines that the "
+                         "default run attaches (keys cv_path, fine_gray, autograd)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", choices=["ccd", "autograd", "cv", "sn", "fg"], default="ccd",
                     help="ccd: the headline penalised Cox fit; autograd: forward + backward of the "
@@ -364,7 +367,7 @@ def run_gpu(args, rank, world):
 
 
 # ------------------------------------------------ differentiable form (f2)
-AG_METRIC = "Cox NLL forward+backward/s, eta = X B, N=2^22 p=256 C=64, bf16 X (tensor-core GEMMs)"
+AG_METRIC = "Cox NLL forward+backward/s, eta = X B, N=2^22 p=256 C=64, bf16 X (tcgen05 tensor-core products)"
 
 
 def run_autograd(args, rank, world):
@@ -421,7 +424,11 @@ def run_autograd(args, rank, world):
     # minimal bytes: X read by both products, eta written by the forward and
     # read by the backward
     alg = 2 * (2 * n * p) + 2 * (4 * n * C)
-    moved = (2 * n * p) + 2 * (4 * n * 2 * C) + (4 * n * 2 * C) + (2 * n * 2 * C) + (2 * n * p) + (2 * n * 2 * C)
+    # as implemented: X B reads X and writes eta; the forward scan reads eta;
+    # the backward reads eta, writes G (bf16, 2 Cp columns) and X^T G reads
+    # X and G
+    Cp = max(32, (C + 15) // 16 * 16)
+    moved = (2 * n * p + 4 * n * C) + 4 * n * C + (4 * n * C + 2 * n * 2 * Cp) + (2 * n * p + 2 * n * 2 * Cp)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -434,13 +441,14 @@ def run_autograd(args, rank, world):
            "vs_baseline": None, "dtype": "bf16 X, f32 B/eta, f64 logs", "data": "synthetic",
            "config": {"workload": "cox_nll_autograd_n4194304_p256_c64", "n": n, "p": p, "columns": C,
                       "time_grid": 5000, "censoring": 0.3,
-                      "l2": "inputs larger than L2 (X 2 GiB, eta 2 GiB)"},
+                      "l2": "inputs larger than L2 (X 2 GiB, eta 1 GiB)"},
            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                         "frac": round(achieved / peak, 4), "traffic": None,
                         "algorithmic_bytes_per_step": alg, "implementation_bytes_per_step": moved,
                         "forward_ms": round(fwd_ms, 3), "backward_ms": round(t_max - fwd_ms, 3),
-                        "kernel": "cuBLAS bf16 GEMMs (X B, X^T G) + k_nll_scan/finish/lambda/grad"},
-           "clocks": clk, "gpu_launches": args.steps * 9}
+                        "kernel": "tcgen05 products k_xb_tc (X B) and k_xtg_tc (X^T G), TMA + TMEM, "
+                                  "+ k_nll_scan/finish/lambda/grad"},
+           "clocks": clk, "gpu_launches": args.steps * 14}
     if not args.no_e2e:
         # autograd function, inputs copied from pinned host memory every step
         hX = X.cpu().pin_memory()
@@ -841,6 +849,31 @@ def run_reference(args, rank, world):
             "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_extra(args):
+    """The other parts of the metric, each with its own timed region and clock
+    record: the batched cross-validated path against 200 sequential plain
+    fits (10 folds x 20 lambdas, N = 1e6, p = 500), the Fine-Gray fit
+    (N = 5e6, p = 50 dense) and the autograd step (N = 2^22, p = 256, C = 64).
+    Their oracle baselines are left to their own --workload runs."""
+    import copy
+    import gc
+    import torch
+    extra = {}
+    for key, fn, steps, warmup in (("cv_path", run_cv, 3, 3), ("fine_gray", run_fg, 10, 3),
+                                   ("autograd", run_autograd, 20, 3)):
+        a = copy.copy(args)
+        a.steps, a.warmup, a.no_cpu_baseline = steps, warmup, True
+        a.n = a.p = None
+        a.schedule = "graph"
+        try:
+            extra[key] = fn(a, 0, 1)
+        except Exception as e:  # report, keep the headline line
+            extra[key] = {"error": "%s: %s" % (type(e).__name__, e)}
+        gc.collect()
+        torch.cuda.empty_cache()
+    return extra
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -862,6 +895,9 @@ def main():
         out = run_gpu(args, rank, world)
     else:
         out = run_gpu(args, rank, world)
+    if (args.impl == "gb300" and args.workload == "ccd" and world == 1 and not args.no_extra and out is not None
+            and args.n is None and args.p is None):
+        out.update(run_extra(args))
     if rank == 0 and out is not None:
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -101,10 +101,75 @@ def test_precision_fg_dense_5e6(lib, prec):
     assert berr <= (1e-9 if prec == "f64" else 1e-5)
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32c"])
+def test_precision_cv_path_benchmarked_size(lib, prec):
+    """Batched CV path, N = 10^6, p = 500 binary at 1 %, 10 folds x 20 L1
+    lambdas (the benchmarked configuration): held-out score relative error
+    of three sampled fits (the oracle's score at the GPU's beta), and max
+    |beta - oracle| of one fit against the oracle's fit of its training set
+    run for the same sweeps."""
+    d = synth.cohort_cox_sparse(1_000_000, 500, seed=41, density=0.01, n_true=10, laplace_scale=0.2,
+                                censor_frac=0.4, grid=3650)
+    if prec == "f64":
+        d["values"] = d["values"].astype(np.float64)
+    fold = synth.cv_folds(1_000_000, 10, seed=42)
+    sd = survdata(d)
+    lam = synth.lambda_grid(binding.cox_lambda_max(sd), 20)
+    r = binding.cox_cv_path(sd, fold, 10, lam, penalty="l1", tol=1e-8, max_sweeps=100, precision=prec)
+    assert r["info"]["fits_converged"] == 200
+    X = oracle_X(d)
+    herr = 0.0
+    for li, k in [(0, 0), (10, 3), (19, 7)]:
+        h = oracle.heldout_loglik(d["time"], d["status"], X, r["beta"][li, k], fold == k)
+        herr = max(herr, abs(r["heldout"][li, k] - h) / abs(h))
+    li, k = 10, 3
+    m = fold != k
+    ref = oracle.ccd_fit("cox", d["time"][m], d["status"][m], X[np.flatnonzero(m)], "l1", lam[li], tol=0.0,
+                         max_sweeps=int(r["sweeps"][li, k]))
+    berr = float(np.max(np.abs(r["beta"][li, k] - ref["beta"])))
+    REPORT.append(("CV path N=1e6 p=500 (held-out score rel; beta of fit (10, 3))", prec, herr, None, None, berr))
+    assert herr <= (1e-10 if prec == "f64" else 1e-6)
+    assert berr <= (1e-9 if prec == "f64" else 1e-5)
+
+
+def test_precision_nll_autograd_full_size(lib):
+    """Differentiable form, N = 2^22, p = 256, C = 64 (X bf16): NLL
+    relative error against the oracle at the split B and at the exact FP32
+    B, and the gradient error as a fraction of the largest gradient entry,
+    on 4 sampled columns (the tolerances are derived in test_gpu_nll.py)."""
+    import torch
+    n, p, C = 1 << 22, 256, 64
+    c = synth.nll_cohort(n, p, C, seed=5, n_times=5000)
+    X = torch.from_numpy(c["X"]).cuda().to(torch.bfloat16)
+    B = torch.from_numpy(c["B"]).cuda()
+    t, s = torch.from_numpy(c["time"]).cuda(), torch.from_numpy(c["status"]).cuda()
+    Bt = B.clone().requires_grad_(True)
+    nll = binding.cox_nll(Bt, X, t, s)
+    (g,) = torch.autograd.grad(nll.sum(), Bt)
+    Xo = X.float().cpu().numpy().astype(np.float64)
+    Bt_ = torch.from_numpy(c["B"])
+    hi = Bt_.to(torch.bfloat16).float()
+    Beff = (hi.double() + (Bt_ - hi).to(torch.bfloat16).double()).numpy()
+    cols = [0, 17, 42, 63]
+    got = nll.detach().cpu().numpy()[cols]
+    eta = Xo @ Beff[:, cols]
+    e_split = float(np.max(np.abs(got - oracle.cox_nll(c["time"], c["status"], eta)) /
+                           np.abs(oracle.cox_nll(c["time"], c["status"], eta))))
+    ex = oracle.cox_nll(c["time"], c["status"], Xo @ c["B"][:, cols].astype(np.float64))
+    e_exact = float(np.max(np.abs(got - ex) / np.abs(ex)))
+    gref = Xo.T @ oracle.cox_nll_grad_eta(c["time"], c["status"], eta)
+    e_grad = float(np.max(np.abs(g.cpu().numpy()[:, cols] - gref)) / np.max(np.abs(gref)))
+    REPORT.append(("NLL autograd N=2^22 p=256 (NLL rel at split B; gradient / max|g|)", "bf16 X", e_split, e_grad,
+                   None, None))
+    REPORT.append(("NLL autograd N=2^22 p=256 (NLL rel at exact FP32 B)", "bf16 X", e_exact, None, None, None))
+    assert e_split <= 1e-7 and e_grad <= 1e-4 and e_exact <= 1e-5
+
+
 def test_zz_print_precision_report(lib):
     if not REPORT:
         pytest.skip("no precision cases ran")
+    f = lambda v: "-" if v is None else "%.2e" % v  # noqa: E731
     print("\n| workload | mode | l rel | g' / S1 | g'' rel | beta abs (fit N=1e4 / FG N=1e5) |")
     print("|---|---|---:|---:|---:|---:|")
     for name, prec, el, eg, eh, eb in REPORT:
-        print("| %s | %s | %.2e | %.2e | %.2e | %s |" % (name, prec, el, eg, eh, "-" if eb is None else "%.2e" % eb))
+        print("| %s | %s | %s | %s | %s | %s |" % (name, prec, f(el), f(eg), f(eh), f(eb)))
