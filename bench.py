@@ -380,7 +380,7 @@ def run_autograd(args, rank, world):
     import __graft_entry__
     __graft_entry__.build()
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
-    n, p, C = 1 << 22, 256, 64
+    n, p, C = args.n or (1 << 22), 256, 64
     c = synth.nll_cohort(n, p, C, seed=5, n_times=5000)
     X = torch.from_numpy(c["X"]).cuda().to(torch.bfloat16)
     B = torch.from_numpy(c["B"]).cuda()
@@ -439,7 +439,7 @@ def run_autograd(args, rank, world):
     out = {"metric": AG_METRIC, "value": round(value, 2), "unit": "steps/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(t_max, 3), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "bf16 X, f32 B/eta, f64 logs", "data": "synthetic",
-           "config": {"workload": "cox_nll_autograd_n4194304_p256_c64", "n": n, "p": p, "columns": C,
+           "config": {"workload": "cox_nll_autograd_n%d_p256_c64" % n, "n": n, "p": p, "columns": C,
                       "time_grid": 5000, "censoring": 0.3,
                       "l2": "inputs larger than L2 (X 2 GiB, eta 1 GiB)"},
            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",

@@ -33,7 +33,8 @@ namespace {
 
 constexpr int kNllThreads = 512;   // scan kernels: two CTAs of 16 warps per SM
 constexpr int kNllMaxCols = 64;    // two columns per lane
-constexpr int kRowsAhead = 4;      // rows whose loads a warp keeps in flight
+constexpr int kRowsAhead = 8;      // rows whose loads a warp of the forward scan keeps in flight
+constexpr int kGradAhead = 4;      // the same for the backward rows (more registers a row)
 
 // B (p x C, row-major FP32) -> Bcat^T (2 Cp rows of ld bf16): row c < C holds
 // hi(B[:, c]), row Cp + c holds lo(B[:, c]) = bf16(B - hi); every other entry
@@ -138,51 +139,48 @@ __global__ void __launch_bounds__(kNllThreads, 2) k_nll_scan(const float* eta, i
   }
 }
 
-// Per column c (one CTA each): prefix of the warp totals in a fixed order,
-// den_k = prefix before the end's warp + rec[k][c] (kept for the backward),
-// NLL_c = -sum delta eta + sum_k d_k log den_k (logs and the sums in FP64).
-__global__ void __launch_bounds__(256) k_nll_finish(const float2* rec, const float2* wt, const float2* wd, int nwarps,
-                                                   int C, const int32_t* gend, const int32_t* dk, int K, int64_t rpw,
-                                                   double* den, double* nll) {
+// Per column c (one CTA of kFinThreads each): prefix of the warp totals in a
+// fixed order (chunk sums, a two-level block scan, the prefix inside each
+// chunk), den_k = prefix before the end's warp + rec[k][c] (kept for the
+// backward), NLL_c = -sum delta eta + sum_k d_k log den_k (logs and the
+// sums in FP64; many threads, because the FP64 logs dominate).
+constexpr int kFinThreads = 1024;
+__global__ void __launch_bounds__(kFinThreads) k_nll_finish(const float2* rec, const float2* wt, const float2* wd,
+                                                          int nwarps, int C, const int32_t* gend, const int32_t* dk,
+                                                          int K, int64_t rpw, double* den, double* nll) {
   extern __shared__ float2 s_base[];  // [nwarps] exclusive prefix (float-float)
-  __shared__ ff s_chunk[256];
-  __shared__ double s_red[8][2];
+  __shared__ ff s_ws[32];
+  __shared__ double s_red[32][2];
   const int c = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  // 1. chunk sums (thread t: warps [t*ch, (t+1)*ch)), then an exclusive scan
-  //    of the 256 chunk sums by one warp, then the prefix inside each chunk
-  const int ch = (nwarps + 255) / 256;
+  const int ch = (nwarps + kFinThreads - 1) / kFinThreads;
   const int w0 = min(tid * ch, nwarps), w1 = min(w0 + ch, nwarps);
   ff cs = ff_zero();
   for (int q = w0; q < w1; ++q) {
     const float2 v = wt[(size_t)q * C + c];
     cs = ff_add(cs, ff{v.x, v.y});
   }
-  s_chunk[tid] = cs;
+  const ff incl = warp_inclusive_scan(cs, lane);
+  if (lane == 31) s_ws[w] = incl;
   __syncthreads();
   if (w == 0) {
-    ff run = ff_zero();
-    for (int q0 = 0; q0 < 256; q0 += 32) {
-      ff v = s_chunk[q0 + lane];
-      ff incl = warp_inclusive_scan(v, lane);
-      ff ex = shfl_up(incl, 1);
-      if (lane == 0) ex = ff_zero();
-      const ff tot = shfl_idx(incl, 31);
-      s_chunk[q0 + lane] = ff_add(run, ex);
-      run = ff_add(run, tot);
-    }
+    const ff t = warp_inclusive_scan(s_ws[lane], lane);
+    const ff ex = shfl_up(t, 1);
+    __syncwarp();
+    s_ws[lane] = lane == 0 ? ff_zero() : ex;
   }
   __syncthreads();
-  ff pre = s_chunk[tid];
+  const ff up = shfl_up(incl, 1);  // every lane takes part in the shuffle
+  ff pre = ff_add(s_ws[w], lane == 0 ? ff_zero() : up);
   for (int q = w0; q < w1; ++q) {
     s_base[q] = make_float2(pre.hi, pre.lo);
     const float2 v = wt[(size_t)q * C + c];
     pre = ff_add(pre, ff{v.x, v.y});
   }
   __syncthreads();
-  // 2. the group ends: den in FP64, d log den
+  // the group ends: den in FP64, d log den
   double sl = 0.0, sd = 0.0;
-  for (int k = tid; k < K; k += 256) {
+  for (int k = tid; k < K; k += kFinThreads) {
     const int q = (int)(gend[k] / rpw);
     const float2 b = s_base[q];
     const float2 r = rec[(size_t)k * C + c];
@@ -191,7 +189,7 @@ __global__ void __launch_bounds__(256) k_nll_finish(const float2* rec, const flo
     den[(size_t)k * C + c] = d;
     if (dk[k] != 0) sl += (double)dk[k] * log(d);
   }
-  for (int q = tid; q < nwarps; q += 256) {
+  for (int q = tid; q < nwarps; q += kFinThreads) {
     const float2 v = wd[(size_t)q * C + c];
     sd += (double)v.x + (double)v.y;
   }
@@ -204,7 +202,7 @@ __global__ void __launch_bounds__(256) k_nll_finish(const float2* rec, const flo
   __syncthreads();
   if (tid == 0) {
     double a = 0.0, b = 0.0;
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < kFinThreads / 32; ++q) {
       a += s_red[q][0];
       b += s_red[q][1];
     }
@@ -264,11 +262,11 @@ __global__ void __launch_bounds__(kNllThreads, 2) k_nll_grad(const float* eta, i
   };
   int64_t cur_end = (int64_t)gend[kn];  // every row < n lies in some group (the last row ends one)
   load_lam();
-  for (int64_t r0 = r_lo; r0 < r_hi; r0 += kRowsAhead) {
-    float v0[kRowsAhead], v1[kRowsAhead];
-    int8_t st[kRowsAhead];
+  for (int64_t r0 = r_lo; r0 < r_hi; r0 += kGradAhead) {
+    float v0[kGradAhead], v1[kGradAhead];
+    int8_t st[kGradAhead];
 #pragma unroll
-    for (int u = 0; u < kRowsAhead; ++u) {
+    for (int u = 0; u < kGradAhead; ++u) {
       const int64_t r = r0 + u;
       const bool in = r < r_hi;
       v0[u] = 0.f;
@@ -277,7 +275,7 @@ __global__ void __launch_bounds__(kNllThreads, 2) k_nll_grad(const float* eta, i
       st[u] = in ? status[r] : (int8_t)0;
     }
 #pragma unroll
-    for (int u = 0; u < kRowsAhead; ++u) {
+    for (int u = 0; u < kGradAhead; ++u) {
       const int64_t r = r0 + u;
       if (r >= r_hi) break;
       if (r > cur_end) {  // past the end of the current group
@@ -452,7 +450,7 @@ int cox_nll_forward(const surv_nll_data* d, const float* B, double* nll, void* s
   if (smem > 48 * 1024)
     NLL_TRY(cuda_err(cudaFuncSetAttribute(k_nll_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                      "smem"));
-  k_nll_finish<<<C, 256, smem, s>>>(static_cast<float2*>(rec), wt2, wt2 + (size_t)nwarps * C, nwarps, C,
+  k_nll_finish<<<C, kFinThreads, smem, s>>>(static_cast<float2*>(rec), wt2, wt2 + (size_t)nwarps * C, nwarps, C,
                                     static_cast<int32_t*>(gend), static_cast<int32_t*>(dk), K, rpw,
                                     static_cast<double*>(den), nll);
   NLL_TRY(cuda_err(cudaGetLastError(), "finish"));

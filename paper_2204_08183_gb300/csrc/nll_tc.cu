@@ -331,19 +331,30 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   }
 }
 
-// grad_B[j][c] = sum over CTAs x (fixed order, FP64) of part[x][j][c] +
-// part[x][j][Cp + c]
-__global__ void k_xtg_reduce(const float* __restrict__ part, int nx, int p, int NB, int C, int Cp,
-                             float* __restrict__ grad_B) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (int64_t)p * C) return;
-  const int j = (int)(i / C), c = (int)(i - (int64_t)j * C);
+// grad_B[j][c] = sum over CTAs x of part[x][j][c] + part[x][j][Cp + c], in
+// FP64 and a fixed order: a block of 32 x 8 threads takes 32 consecutive
+// outputs (coalesced along c); thread row y sums the CTAs x = y, y + 8, ...
+// and row 0 adds the 8 row sums in order.
+constexpr int kRedX = 32, kRedY = 8;
+__global__ void __launch_bounds__(kRedX * kRedY) k_xtg_reduce(const float* __restrict__ part, int nx, int p, int NB,
+                                                              int C, int Cp, float* __restrict__ grad_B) {
+  __shared__ double s[kRedY][kRedX];
+  const int64_t i = (int64_t)blockIdx.x * kRedX + threadIdx.x;
+  const bool in = i < (int64_t)p * C;
+  const int j = in ? (int)(i / C) : 0, c = in ? (int)(i - (int64_t)j * C) : 0;
   double a = 0.0;
-  for (int x = 0; x < nx; ++x) {
-    const float* r = part + ((size_t)x * p + j) * NB;
-    a += (double)r[c] + (double)r[Cp + c];
+  if (in)
+    for (int x = threadIdx.y; x < nx; x += kRedY) {
+      const float* r = part + ((size_t)x * p + j) * NB;
+      a += (double)r[c] + (double)r[Cp + c];
+    }
+  s[threadIdx.y][threadIdx.x] = a;
+  __syncthreads();
+  if (threadIdx.y == 0 && in) {
+    double t = s[0][threadIdx.x];
+    for (int y = 1; y < kRedY; ++y) t += s[y][threadIdx.x];
+    grad_B[i] = (float)t;
   }
-  grad_B[i] = (float)a;
 }
 
 // ----------------------------------------------------------------- host
@@ -459,7 +470,7 @@ cudaError_t nll_xtg_tc(const void* X, int64_t n, int p, int64_t ldx, const void*
   st = cudaGetLastError();
   if (st != cudaSuccess) return st;
   const int64_t pc = (int64_t)p * C;
-  k_xtg_reduce<<<(unsigned)((pc + 255) / 256), 256, 0, s>>>(part, nx, p, NB, C, Cp, grad_B);
+  k_xtg_reduce<<<(unsigned)((pc + kRedX - 1) / kRedX), dim3(kRedX, kRedY), 0, s>>>(part, nx, p, NB, C, Cp, grad_B);
   return cudaGetLastError();
 }
 
