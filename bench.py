@@ -78,7 +78,7 @@ def parse():
 
 # Steady-state DRAM bytes per row pass of the headline kernels (ncu capture
 # of the committed k_ipass<4> + k_itrans<4>; None until captured).
-TRAFFIC_IND_ROW_PASS = None
+TRAFFIC_IND_ROW_PASS = 18556774
 
 
 def workload(n, p):
