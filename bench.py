@@ -247,10 +247,14 @@ def run_gpu(args, rank, world):
     row_passes = sum(i["row_passes"] for i in infos)
     batched = (not sn) and args.schedule == "graph" and row_passes < passes
     if batched:
-        # speculative batches: a row pass reads e once and the slices of up
-        # to 4 columns (counted as 4: an upper bound on the columns read)
-        per_row_pass = 4 * n + args.spec_b * (4 + vb) * nnz / p + 8 * K
-        alg_bytes = row_passes * per_row_pass + upd * per_update
+        # speculative batches: a row pass reads the slices of up to B columns
+        # (counted as B: an upper bound on the columns read) and the group
+        # table; it streams e only when e has changed since the previous
+        # pass (after a nonzero step, and at the first pass of a fit):
+        # otherwise the stored sums of e are reused
+        per_row_pass = args.spec_b * (4 + vb) * nnz / p + 8 * K
+        dense_passes = min(row_passes, upd + len(infos))
+        alg_bytes = row_passes * per_row_pass + dense_passes * 4 * n + upd * per_update
     if sn:
         # per coordinate: column j (row, value) and, per nonzero, e, its
         # group, Lambda and W (4 + 4 + 8 + 8); per rebuild of the risk sets
@@ -286,6 +290,7 @@ def run_gpu(args, rank, world):
             roofline["traffic"] = TRAFFIC_IND_ROW_PASS
             roofline["traffic_note"] = "bytes per row pass, ncu steady-state capture of the kernels as committed"
         roofline["algorithmic_bytes_per_row_pass"] = round(alg_bytes / row_passes)
+        roofline["row_passes_streaming_e_per_fit"] = dense_passes / len(infos)
         roofline["us_per_row_pass"] = round(kern_ms * 1e3 / row_passes, 3)
     if batched:
         roofline.setdefault("traffic", None)

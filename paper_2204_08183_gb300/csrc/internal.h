@@ -107,7 +107,8 @@ struct alignas(128) CtlLine {
   double f_prev;         // objective at the latest evaluation
   long long passes;      // coordinate passes so far
   long long eta_updates; // nonzero steps so far
-  int32_t dirty;         // sparse-numerator form: the risk-set sums are stale
+  int32_t dirty;         // the stored risk-set sums of e are stale (set at the start of a fit; sparse-
+                         //   numerator form and speculative batches)
   int32_t j0;            // speculative batches: first coordinate of the next batch
   int32_t q;             //   and the coordinate whose step is still to be applied (-1: none)
   long long batches;     //   and the row passes so far

@@ -154,7 +154,7 @@ template <int B>
 __global__ void __launch_bounds__(kSpNT, 2) k_spass(const __grid_constant__ CcdParams P, int slot) {
   constexpr int R = SpCfg<B>::R;
   __shared__ ff s_wtot[kMaxWarpsPerCta][R];
-  __shared__ int s_stop, s_j0, s_q;
+  __shared__ int s_stop, s_j0, s_q, s_dirty;
   __shared__ double s_applied;
   __shared__ float s_delta[2];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -177,11 +177,15 @@ __global__ void __launch_bounds__(kSpNT, 2) k_spass(const __grid_constant__ CcdP
     s_applied = __ldcg(&L->applied);
     s_delta[0] = __ldcg(&L->delta_hi);
     s_delta[1] = __ldcg(&L->delta_lo);
+    s_dirty = __ldcg(&L->dirty);
   }
   __syncthreads();
   if (s_stop) return;
   const int j0 = s_j0;
   const int nb = min(B, P.p - j0);
+  // e unchanged since the previous pass (zero pending step): its stored
+  // prefix of e, warp offsets and CTA aggregate of component 0 still hold
+  const bool dense = s_applied != 0.0 || s_dirty != 0;
   // the batch's column slices in this warp's rows (their loads overlap the
   // update and the dense walk)
   const int nw1 = P.nwarps + 1;
@@ -197,7 +201,7 @@ __global__ void __launch_bounds__(kSpNT, 2) k_spass(const __grid_constant__ CcdP
   if (s_applied != 0.0) warp_update<0, float>(P, s_q, gw, row_lo, row_hi, s_applied, ff{s_delta[0], s_delta[1]});
   ff* rec = reinterpret_cast<ff*>(P.rec);
   const float* e = reinterpret_cast<const float*>(P.e);
-  {
+  if (dense) {
     ff t0[1] = {sp_dense(e, P.gend, row_lo, row_hi, rec, R, EndCursor{k_lo, k_hi, k_lo, kreg})};
     warp_sum_some<1>(t0);
     if (lane == 0) s_wtot[w][0] = t0[0];
@@ -232,7 +236,8 @@ __global__ void __launch_bounds__(kSpNT, 2) k_spass(const __grid_constant__ CcdP
   pdl_launch_dependents();
   __syncthreads();
   // warp w scans component m = w, w + WPC, ... over the CTA's warps
-  for (int m = w; m < R; m += WPC) {
+  // (component 0 only after a dense walk)
+  for (int m = dense ? w : w + 1; m < R; m += WPC) {
     ff v = ff_zero();
     if (lane < WPC) v = s_wtot[lane][m];
     const ff incl = warp_inclusive_scan(v, lane);
@@ -350,6 +355,7 @@ __device__ __forceinline__ void commit_batch(const CcdParams& P, const LineView&
   L->j0 = stop ? j0 : j0n;
   L->q = (nz && !stop) ? j0 + bstar : -1;
   L->batches = batches;
+  L->dirty = 0;  // the batch's pass stored the sums of e at the current e
   if (lane == 0) ctl->ticket = 0u;
 }
 
@@ -612,7 +618,7 @@ template <int B>
 __global__ void __launch_bounds__(kSpNT, 2) k_ipass(const __grid_constant__ CcdParams P, int slot) {
   constexpr int R = IpCfg<B>::R, RP = IpCfg<B>::RP, SR = IpCfg<B>::SR;
   __shared__ ff s_wtot[kMaxWarpsPerCta][R];
-  __shared__ int s_stop, s_j0, s_q;
+  __shared__ int s_stop, s_j0, s_q, s_dirty;
   __shared__ double s_applied;
   __shared__ float s_delta[2];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -634,11 +640,18 @@ __global__ void __launch_bounds__(kSpNT, 2) k_ipass(const __grid_constant__ CcdP
     s_applied = __ldcg(&L->applied);
     s_delta[0] = __ldcg(&L->delta_hi);
     s_delta[1] = __ldcg(&L->delta_lo);
+    s_dirty = __ldcg(&L->dirty);
   }
   __syncthreads();
   if (s_stop) return;
   const int j0 = s_j0;
   const int nb = min(B, P.p - j0);
+  // e changes only through a nonzero step: when the pending step is zero
+  // (and the fit has passed its first batch) e is the e of the previous
+  // pass, and so are the prefix of e at the group ends, the warp offsets and
+  // the CTA aggregate of that component, which stay where that pass stored
+  // them, bit for bit
+  const bool dense = s_applied != 0.0 || s_dirty != 0;
   const int nw1 = P.nwarps + 1;
   const int32_t* col[B];
   int len[B];
@@ -656,7 +669,7 @@ __global__ void __launch_bounds__(kSpNT, 2) k_ipass(const __grid_constant__ CcdP
   int row0[B][SR];
   ip_first_rows<B, SR>(col, len, row0);
   ff tot[RP];
-  tot[0] = sp_dense(e, P.gend, row_lo, row_hi, rec, R, EndCursor{k_lo, k_hi, k_lo, kreg});
+  tot[0] = dense ? sp_dense(e, P.gend, row_lo, row_hi, rec, R, EndCursor{k_lo, k_hi, k_lo, kreg}) : ff_zero();
   int kn[B];
   {
     ff acc[B];
@@ -669,7 +682,7 @@ __global__ void __launch_bounds__(kSpNT, 2) k_ipass(const __grid_constant__ CcdP
   warp_reduce_scatter<RP>(tot, lane);
   const int comp = warp_rs_component<RP>(lane);
   if (comp < R && lane == warp_rs_lane<RP>(comp)) {
-    s_wtot[w][comp] = tot[0];
+    s_wtot[w][comp] = tot[0];  // component 0 is used only when the dense walk ran
     // group ends after the column's last nonzero in the warp's rows see the
     // warp total
     if (comp >= 1) {
@@ -682,8 +695,9 @@ __global__ void __launch_bounds__(kSpNT, 2) k_ipass(const __grid_constant__ CcdP
   }
   pdl_launch_dependents();
   __syncthreads();
-  // warp m scans component m over the CTA's warps
-  for (int m = w; m < R; m += WPC) {
+  // warp m scans component m over the CTA's warps (component 0 only after
+  // a dense walk)
+  for (int m = dense ? w : w + 1; m < R; m += WPC) {
     ff v = ff_zero();
     if (lane < WPC) v = s_wtot[lane][m];
     const ff incl = warp_inclusive_scan(v, lane);
