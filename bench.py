@@ -241,9 +241,12 @@ def run_gpu(args, rank, world):
     # reads only the row indices of a column
     ind = d["values"] is None or bool(np.all(d["values"] == 1))
     vb = 0 if ind else 4                              # bytes of a value per nonzero
-    per_pass = 4 * n + (4 + vb) * nnz / p + 8 * K     # e stream + column j (row, value) + group table
+    # per coordinate: column j (row, value) + group table; e is streamed only
+    # when it changed since the previous pass (after a nonzero step, and at
+    # the first pass of a fit), otherwise the stored sums of e are reused
+    per_pass = (4 + vb) * nnz / p + 8 * K
     per_update = (24 + vb) * nnz / p                  # row, value, eta r/w (8+8), e write
-    alg_bytes = passes * per_pass + upd * per_update
+    alg_bytes = passes * per_pass + min(passes, upd + len(infos)) * 4 * n + upd * per_update
     row_passes = sum(i["row_passes"] for i in infos)
     batched = (not sn) and args.schedule == "graph" and row_passes < passes
     if batched:
@@ -563,9 +566,12 @@ def run_cv(args, rank, world):
     K = infos[-1]["n_groups"]
     passes = sum(i["coordinate_passes"] for i in infos)
     upd = sum(i["eta_updates"] for i in infos)
-    per_pass = 4 * n + 8 * nnz / p + 8 * K
-    per_update = 28 * nnz / p
-    alg = passes * per_pass + upd * per_update
+    # column j's row indices (indicator data: no values) and the group table
+    # per coordinate; e over all N rows only after a nonzero step and at each
+    # fit's first pass (otherwise its stored sums are reused)
+    per_pass = 4 * nnz / p + 8 * K
+    per_update = 24 * nnz / p
+    alg = passes * per_pass + min(passes, upd + F * len(infos)) * 4 * n + upd * per_update
     kern_ms = sum(i["ccd_kernel_ms"] for i in infos)
     peaks = {}
     try:

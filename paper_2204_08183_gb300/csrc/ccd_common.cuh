@@ -196,10 +196,14 @@ struct EndCursor {
 // (and X, W) in tiles of 32 * U * VEC rows; the CSC components walk the
 // column's nonzeros in the warp's rows (woff holds the per-warp offsets).
 template <int MODEL, int LAYOUT, typename T, int U_, int SR, bool MULTI = false>
+// dense = false (CSC only): e has not changed since the previous pass of the
+// fit, so the dense components (e, and for Fine-Gray W e), their records at
+// the group ends and their totals are the stored ones; they are neither
+// recomputed nor written (tot gets zeros for them).
 __device__ __forceinline__ void warp_pass(const CcdParams& P, int j, int64_t row_lo, int64_t row_hi,
                                           typename AccOf<T>::type* rec,
                                           typename AccOf<T>::type (&tot)[Cfg<MODEL, LAYOUT, T>::M],
-                                          const PassPrefetch<T, SR>& pf) {
+                                          const PassPrefetch<T, SR>& pf, bool dense = true) {
   using A = typename AccOf<T>::type;
   using C = Cfg<MODEL, LAYOUT, T>;
   constexpr int M = C::M;
@@ -214,7 +218,7 @@ __device__ __forceinline__ void warp_pass(const CcdParams& P, int j, int64_t row
   const uint64_t keep = l2_keep(), strm = l2_stream();
 #pragma unroll
   for (int m = 0; m < M; ++m) acc_zero(tot[m]);
-  {
+  if (LAYOUT == 1 || dense) {
     A acc[ND];
 #pragma unroll
     for (int d = 0; d < ND; ++d) acc_zero(acc[d]);

@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(GCfg<MODEL, LAYOUT>::NT, GCfg<MODEL, LAYOUT>::
   using C = Cfg<MODEL, LAYOUT, T>;
   constexpr int M = C::M;
   __shared__ A s_wtot[kMaxWarpsPerCta][M];
-  __shared__ int s_stop;
+  __shared__ int s_stop, s_dirty;
   __shared__ double s_applied;
   __shared__ float s_delta[2];
   __shared__ CcdParams s_fit;
@@ -124,16 +124,21 @@ __global__ void __launch_bounds__(GCfg<MODEL, LAYOUT>::NT, GCfg<MODEL, LAYOUT>::
     s_applied = __ldcg(&L->applied);
     s_delta[0] = __ldcg(&L->delta_hi);
     s_delta[1] = __ldcg(&L->delta_lo);
+    s_dirty = __ldcg(&L->dirty);
   }
   __syncthreads();
   if (s_stop) return;  // the same value in every CTA
   const double applied = s_applied;
   if (applied != 0.0) warp_update<LAYOUT, T>(P, q, gw, row_lo, row_hi, applied, ff{s_delta[0], s_delta[1]});
+  // CSC: with a zero pending step e is the e of the previous coordinate's
+  // pass (after the fit's first pass), and so are the sums of its dense
+  // components, stored by that pass; they are reused bit for bit
+  const bool dense = LAYOUT == 1 || applied != 0.0 || s_dirty != 0;
 
   // ------------------------------------------- step 2 for coordinate j
   A* rec = reinterpret_cast<A*>(P.rec);
   A tot[M];
-  warp_pass<MODEL, LAYOUT, T, GC::U, GC::SR, MULTI>(P, j, row_lo, row_hi, rec, tot, pf);
+  warp_pass<MODEL, LAYOUT, T, GC::U, GC::SR, MULTI>(P, j, row_lo, row_hi, rec, tot, pf, dense);
   pdl_launch_dependents();
   if (lane == 0)
 #pragma unroll
@@ -151,14 +156,17 @@ __global__ void __launch_bounds__(GCfg<MODEL, LAYOUT>::NT, GCfg<MODEL, LAYOUT>::
     warp_scan_n<M>(v, lane);
 #pragma unroll
     for (int m = 0; m < M; ++m) {
+      // the stored values of the dense CSC components stay when they were reused
+      const bool keep = LAYOUT == 0 && !dense && (m == 0 || m == 3);
       A ex = shfl_up(v[m], 1);
       if (lane == 0) acc_zero(ex);
-      if (lane < WPC) P.wt[(size_t)m * P.nwarps + c * WPC + lane] = pack8(ex);
+      if (lane < WPC && !keep) P.wt[(size_t)m * P.nwarps + c * WPC + lane] = pack8(ex);
       v[m] = shfl_idx(v[m], WPC - 1);
     }
     if (lane < kRep)
 #pragma unroll
-      for (int m = 0; m < M; ++m) P.agg[((size_t)lane * M + m) * G + c] = pack8(v[m]);
+      for (int m = 0; m < M; ++m)
+        if (!(LAYOUT == 0 && !dense && (m == 0 || m == 3))) P.agg[((size_t)lane * M + m) * G + c] = pack8(v[m]);
   }
 }
 
