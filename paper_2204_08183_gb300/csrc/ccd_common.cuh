@@ -200,10 +200,15 @@ template <int MODEL, int LAYOUT, typename T, int U_, int SR, bool MULTI = false>
 // fit, so the dense components (e, and for Fine-Gray W e), their records at
 // the group ends and their totals are the stored ones; they are neither
 // recomputed nor written (tot gets zeros for them).
+// xq (dense X, FP32 only): the pending step delta of the column xq is applied
+// in the same sweep over the warp's rows: each tile loads eta and x_q
+// instead of e, writes eta + delta x_q and its e (the arithmetic of
+// warp_update, element for element) and passes the new e on; null: e is read.
 __device__ __forceinline__ void warp_pass(const CcdParams& P, int j, int64_t row_lo, int64_t row_hi,
                                           typename AccOf<T>::type* rec,
                                           typename AccOf<T>::type (&tot)[Cfg<MODEL, LAYOUT, T>::M],
-                                          const PassPrefetch<T, SR>& pf, bool dense = true) {
+                                          const PassPrefetch<T, SR>& pf, bool dense = true,
+                                          const T* xq = nullptr, ff delta = ff{0.f, 0.f}) {
   using A = typename AccOf<T>::type;
   using C = Cfg<MODEL, LAYOUT, T>;
   constexpr int M = C::M;
@@ -229,6 +234,62 @@ __device__ __forceinline__ void warp_pass(const CcdParams& P, int j, int64_t row
     // loads of one tile from global memory (16-byte loads; the last partial
     // tile element by element)
     auto load_tile = [&](int64_t t0, T (&ev)[U][VEC], T (&xv)[U][VEC], T (&wv)[U][VEC]) {
+      if constexpr (LAYOUT == 1 && sizeof(T) == 4) {
+        if (xq) {
+          // fused update of the pending step (FP32 mode: eta float-float)
+          float2* etap = reinterpret_cast<float2*>(P.eta);
+          float* ep = reinterpret_cast<float*>(P.e);
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int64_t r = t0 + (int64_t)(lane + 32 * u) * VEC;
+            float xx[VEC];
+            float2 qq[VEC];
+            if (r + VEC <= row_hi) {
+              ld4_hint(reinterpret_cast<const float*>(xq) + r, strm, xx);
+              const float4 a = *reinterpret_cast<const float4*>(etap + r);
+              const float4 b = *reinterpret_cast<const float4*>(etap + r + 2);
+              qq[0] = make_float2(a.x, a.y);
+              qq[1] = make_float2(a.z, a.w);
+              qq[2] = make_float2(b.x, b.y);
+              qq[3] = make_float2(b.z, b.w);
+              ld4_hint(xcol + r, strm, xv[u]);
+              if (MODEL == 1) ld4_hint(w2 + r, keep, wv[u]);
+            } else {
+#pragma unroll
+              for (int q = 0; q < VEC; ++q) {
+                const bool in = r + q < row_hi;
+                xx[q] = in ? reinterpret_cast<const float*>(xq)[r + q] : 0.f;
+                qq[q] = in ? etap[r + q] : make_float2(0.f, 0.f);
+                xv[u][q] = in ? xcol[r + q] : T(0);
+                wv[u][q] = (MODEL == 1 && in) ? w2[r + q] : T(0);
+              }
+            }
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) {
+              const ff v = ff_add({qq[q].x, qq[q].y}, ff_mul_f(delta, xx[q]));
+              qq[q] = make_float2(v.hi, v.lo);
+              const float ex = expf(v.hi);
+              // rows past the warp's range take no part (e = 0), as in the plain loads
+              const bool in = r + q < row_hi;
+              const bool held = in && P.fold_id && P.fold_id[r + q] == P.fold;
+              ev[u][q] = (!in || held) ? 0.f : fmaf(ex, v.lo, ex);
+            }
+            if (r + VEC <= row_hi) {
+              *reinterpret_cast<float4*>(etap + r) = make_float4(qq[0].x, qq[0].y, qq[1].x, qq[1].y);
+              *reinterpret_cast<float4*>(etap + r + 2) = make_float4(qq[2].x, qq[2].y, qq[3].x, qq[3].y);
+              *reinterpret_cast<float4*>(ep + r) = make_float4(ev[u][0], ev[u][1], ev[u][2], ev[u][3]);
+            } else {
+#pragma unroll
+              for (int q = 0; q < VEC; ++q)
+                if (r + q < row_hi) {
+                  etap[r + q] = qq[q];
+                  ep[r + q] = ev[u][q];
+                }
+            }
+          }
+          return;
+        }
+      }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int64_t r = t0 + (int64_t)(lane + 32 * u) * VEC;

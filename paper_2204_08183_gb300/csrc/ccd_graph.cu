@@ -129,16 +129,21 @@ __global__ void __launch_bounds__(GCfg<MODEL, LAYOUT>::NT, GCfg<MODEL, LAYOUT>::
   __syncthreads();
   if (s_stop) return;  // the same value in every CTA
   const double applied = s_applied;
-  if (applied != 0.0) warp_update<LAYOUT, T>(P, q, gw, row_lo, row_hi, applied, ff{s_delta[0], s_delta[1]});
+  // dense X in the FP32 mode: the update rides along the row pass (one sweep
+  // over the warp's rows); otherwise it runs first
+  constexpr bool kFuse = LAYOUT == 1 && sizeof(T) == 4;
+  if (applied != 0.0 && !kFuse) warp_update<LAYOUT, T>(P, q, gw, row_lo, row_hi, applied, ff{s_delta[0], s_delta[1]});
   // CSC: with a zero pending step e is the e of the previous coordinate's
   // pass (after the fit's first pass), and so are the sums of its dense
   // components, stored by that pass; they are reused bit for bit
   const bool dense = LAYOUT == 1 || applied != 0.0 || s_dirty != 0;
+  const T* xq = (kFuse && applied != 0.0) ? reinterpret_cast<const T*>(P.X) + (size_t)q * P.ld : nullptr;
 
   // ------------------------------------------- step 2 for coordinate j
   A* rec = reinterpret_cast<A*>(P.rec);
   A tot[M];
-  warp_pass<MODEL, LAYOUT, T, GC::U, GC::SR, MULTI>(P, j, row_lo, row_hi, rec, tot, pf, dense);
+  warp_pass<MODEL, LAYOUT, T, GC::U, GC::SR, MULTI>(P, j, row_lo, row_hi, rec, tot, pf, dense, xq,
+                                                    ff{s_delta[0], s_delta[1]});
   pdl_launch_dependents();
   if (lane == 0)
 #pragma unroll
