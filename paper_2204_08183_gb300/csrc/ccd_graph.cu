@@ -48,7 +48,7 @@ template <int MODEL, int LAYOUT>
 struct GCfg {
   static constexpr int NT = 512;
   static constexpr int MINB = 2;
-  static constexpr int U = MODEL == 1 ? 2 : 4;
+  static constexpr int U = (MODEL == 1 && LAYOUT == 1) ? 1 : (MODEL == 1 ? 2 : 4);
   static constexpr int SR = 4;
 };
 constexpr int kTransThreads = 256;
