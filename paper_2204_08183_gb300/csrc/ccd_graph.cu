@@ -413,6 +413,211 @@ __global__ void __launch_bounds__(kTransThreads) k_trans(const __grid_constant__
                  s_lin[1], acc_to_d(s_red[0][2]), s_next);
 }
 
+// Transform of single fits with the work spread evenly: every CTA scans the
+// pass CTAs' aggregates (one per thread, two-level warp scans in shared
+// memory; Fine-Gray also takes the grand totals of the suffix components)
+// and takes an even share of the group ends, about one a thread.  The
+// per-CTA range split of k_trans gave the CTAs holding the first rows (many
+// small tie groups) most of the work.  It reads the control line and its
+// first end's group table entries before the wait: the line was written by
+// the previous coordinate's transform, which finished before this
+// coordinate's pass kernel passed its own wait.
+constexpr int kBtNT = 512;
+constexpr int kBtWarps = kBtNT / 32;
+
+template <int MODEL, int LAYOUT, typename T>
+__global__ void __launch_bounds__(kBtNT) k_btrans(const __grid_constant__ CcdParams P, int j) {
+  using A = typename AccOf<T>::type;
+  constexpr int M = MODEL == 0 ? 3 : 6;
+  __shared__ A s_T[kBtNT][M];
+  __shared__ A s_w[kBtWarps][M];
+  __shared__ A s_tot3[3];
+  __shared__ A s_red[kBtWarps][3];
+  __shared__ int s_last, s_stop;
+  __shared__ double s_lin[2];
+  __shared__ double s_next[4];
+  GraphCtl* ctl = P.gctl;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int WPC = P.wpc, G = P.G, G2 = gridDim.x, c2 = blockIdx.x;
+  const bool eval = j == 0;
+  LineView lv;
+  if (tid == 0) {
+    lv = load_line(ctl, c2);
+    s_stop = lv.stop;
+  }
+  const int stride = G2 * kBtNT;
+  const int k0 = c2 * kBtNT + tid;
+  int d1 = 0, gw1 = 0;
+  double g1 = 0.0;
+  float2 gf1 = make_float2(0.f, 0.f);
+  if (k0 < P.K) {
+    d1 = P.dk[k0];
+    gw1 = (int)((P.gend[k0] >> 5) / P.wpw);
+    if (MODEL == 1) {
+      g1 = P.Gk[k0];
+      gf1 = P.Gkff[k0];
+    }
+  }
+  __syncthreads();
+  if (s_stop) {  // the same value in every CTA
+    pdl_wait();
+    return;
+  }
+  pdl_wait();
+
+  // exclusive prefix over the pass CTAs of their aggregates, fixed order
+  {
+    const uint64_t* agg = P.agg + (size_t)(c2 % kRep) * M * G;
+    A v[M], incl[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      acc_zero(v[m]);
+      if (tid < G) v[m] = unpack8<A>(__ldcg(agg + (size_t)m * G + tid));
+      incl[m] = v[m];
+    }
+    warp_scan_n<M>(incl, lane);
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      const A ex = shfl_up(incl[m], 1);
+      if (lane == 0) acc_zero(v[m]);
+      else v[m] = ex;
+    }
+    if (lane == 31)
+#pragma unroll
+      for (int m = 0; m < M; ++m) s_w[w][m] = incl[m];
+    __syncthreads();
+    if (w == 0) {
+      A t[M];
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        acc_zero(t[m]);
+        if (lane < kBtWarps) t[m] = s_w[lane][m];
+      }
+      warp_scan_n<M>(t, lane);
+      __syncwarp();
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        const A ex = shfl_up(t[m], 1);
+        const A all = shfl_idx(t[m], kBtWarps - 1);
+        if (lane < kBtWarps) {
+          if (lane == 0) acc_zero(s_w[lane][m]);
+          else s_w[lane][m] = ex;
+        }
+        if (MODEL == 1 && m >= 3 && lane == 0) s_tot3[m % 3] = all;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < M; ++m) s_T[tid][m] = acc_add(s_w[w][m], v[m]);
+  }
+  __syncthreads();
+
+  // steps 3-4 at the group ends
+  A fg1, fg2;
+  acc_zero(fg1);
+  acc_zero(fg2);
+  double pl = 0.0;
+  A tot3[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    acc_zero(tot3[i]);
+    if (MODEL == 1) tot3[i] = s_tot3[i];
+  }
+  const A* rec = reinterpret_cast<const A*>(P.rec);
+  for (int k = k0; k < P.K; k += stride) {
+    int d, gwk;
+    double g;
+    float2 gf;
+    if (k == k0) {
+      d = d1, gwk = gw1, g = g1, gf = gf1;
+    } else {
+      d = P.dk[k];
+      gwk = (int)((P.gend[k] >> 5) / P.wpw);
+      g = MODEL == 1 ? P.Gk[k] : 0.0;
+      gf = MODEL == 1 ? P.Gkff[k] : make_float2(0.f, 0.f);
+    }
+    if (d == 0) continue;
+    const int f = gwk / WPC;
+    A Pm[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m)
+      Pm[m] = acc_add(acc_add(s_T[f][m], unpack8<A>(__ldcg(P.wt + (size_t)m * P.nwarps + gwk))),
+                      rec[(size_t)k * M + m]);
+    A den = Pm[0], num1 = Pm[1], num2 = Pm[2];
+    if (MODEL == 1) {
+      // the competing-event suffix strictly after the end, weighted by G(t_k)
+      const A gg = acc_base<A>(g, ff{gf.x, gf.y});
+      den = acc_add(den, acc_mul(gg, acc_add(tot3[0], acc_neg(Pm[3 % M]))));
+      num1 = acc_add(num1, acc_mul(gg, acc_add(tot3[1], acc_neg(Pm[4 % M]))));
+      num2 = acc_add(num2, acc_mul(gg, acc_add(tot3[2], acc_neg(Pm[5 % M]))));
+    }
+    const A inv = acc_recip(den);
+    const A Gr = acc_mul(num1, inv);
+    const A H = acc_mul(num2, inv);
+    fg1 = acc_add(fg1, acc_scale(Gr, d));
+    fg2 = acc_add(fg2, acc_scale(acc_add(H, acc_neg(acc_mul(Gr, Gr))), d));
+    if (eval) pl += (double)d * log(acc_to_d(den));
+  }
+
+  // CTA partials, fixed order
+  {
+    A r[3] = {fg1, fg2, eval ? acc_from_d(pl, (A*)nullptr) : A{}};
+    warp_sum_n<3>(r);
+    if (lane == 0)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) s_red[w][i] = r[i];
+  }
+  __syncthreads();
+  uint64_t* part = reinterpret_cast<uint64_t*>(P.slot_part);
+  if (tid < 3) {
+    A a = s_red[0][tid];
+#pragma unroll 1
+    for (int qw = 1; qw < kBtWarps; ++qw) a = acc_add(a, s_red[qw][tid]);
+    part[(size_t)tid * G2 + c2] = pack8(a);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    unsigned prev;
+    asm volatile("atom.add.release.gpu.u32 %0, [%1], 1;" : "=r"(prev) : "l"(&ctl->ticket) : "memory");
+    s_last = prev == (unsigned)(G2 - 1);
+  }
+  pdl_launch_dependents();
+  __syncthreads();
+  if (!s_last) return;
+
+  // ------------------------------- last CTA: the step of coordinate j
+  if (w < 3) {
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    A acc;
+    acc_zero(acc);
+    for (int qc = lane; qc < G2; qc += 32) acc = acc_add(acc, unpack8<A>(__ldcg(part + (size_t)w * G2 + qc)));
+    A r[1] = {acc};
+    warp_sum_n<1>(r);
+    if (lane == 0) s_red[0][w] = r[0];
+  } else if (w == 3 && eval) {
+    double lin, pen;
+    warp_lin_pen(P, -1, 0.0, lin, pen);
+    if (lane == 0) {
+      s_lin[0] = lin;
+      s_lin[1] = pen;
+    }
+  } else if (w == 4 && lane == 0) {
+    const int jn = j + 1 < P.p ? j + 1 : 0;
+    s_next[0] = __ldcg(P.beta + jn);
+    s_next[1] = __ldcg(P.width + jn);
+    s_next[2] = P.pen[jn];
+    s_next[3] = P.dTx[jn];
+  }
+  __syncthreads();
+  if (w == 0)
+    publish_step(P, j, lv, lv.dtx - acc_to_d(s_red[0][0]), -acc_to_d(s_red[0][1]), eval, s_lin[0], s_lin[1],
+                 acc_to_d(s_red[0][2]), s_next);
+}
+
+// CTAs of the balanced transform: about one group end a thread, 4 to 152.
+inline int btrans_ctas(int K) { return std::max(4, std::min(152, (K + kBtNT - 1) / kBtNT)); }
+
 // Grid of the pass kernel: as many CTAs per SM (up to MINB) as fit.
 template <int MODEL, int LAYOUT, typename T>
 cudaError_t grid_graph(int* G, int* wpc) {
@@ -467,6 +672,13 @@ cudaError_t capture_sweep(const CcdParams& P, bool pdl, cudaStream_t cs, cudaGra
       if (junk) cudaGraphDestroy(junk);
       return cudaErrorInvalidValue;
     }
+  }
+  // single fits: the balanced transform (one pass-CTA aggregate per thread
+  // in its scan, so up to kBtNT pass CTAs)
+  if (P.nfit == 0 && P.G <= kBtNT) {
+    kt = k_btrans<MODEL, LAYOUT, T>;
+    ct.gridDim = dim3(btrans_ctas(P.K));
+    ct.blockDim = dim3(kBtNT);
   }
   cudaError_t lst = cudaSuccess;
   for (int j = 0; j < P.p && lst == cudaSuccess; ++j) {
