@@ -533,7 +533,8 @@ def run_cv(args, rank, world):
     clocks.start()
     time.sleep(1.5)
     for w in range(args.warmup):
-        # the first warm-up call tunes the CTAs per fit (kept in the workspace)
+        # the first warm-up call tunes the CTAs per fit and the row-pass form
+        # (kept in the workspace)
         tune = binding.SURV_FLAG_CV_TUNE if (w == 0 and args.ctas == 0) else 0
         binding.cox_cv_path(sd, fold_d, 10, lam, flags=tune, **kw)
     torch.cuda.synchronize()
@@ -589,7 +590,9 @@ def run_cv(args, rank, world):
                       "lambdas": 20, "lambda_max": lmax, "lambda_ratio": 1e-3, "tol": 1e-8, "censoring": 0.4,
                       "time_grid": 3650, "start": "cold (beta = 0) for every fit",
                       "ctas_per_fit": infos[-1]["ctas_per_fit"],
-                      "ctas_source": "autotuned (one timed sweep per candidate, first warm-up call)"
+                      "row_pass_form": {1: "one warp reduction per group end",
+                                        2: "lane scans per tile"}[infos[-1]["row_pass_form"]],
+                      "ctas_source": "autotuned with the row-pass form (one timed sweep per candidate, first warm-up call)"
                       if args.ctas == 0 else "--ctas",
                       "l2": "inputs larger than L2 (e + eta of 200 fits: 2.4 GB)"},
            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",

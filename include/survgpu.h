@@ -129,9 +129,11 @@ typedef struct surv_opts {
  * uses the persistent kernel. */
 #define SURV_FLAG_PERSISTENT 2
 /* cox_cv_path only, with ctas_per_fit = 0: time one sweep of the batched
- * schedule for each of a few CTA-per-fit counts around the default (every
- * candidate from the same cold start), run the path with the fastest, and
- * keep that count in the workspace for later calls with the same shape
+ * schedule for each of a few CTA-per-fit counts around the default and, for
+ * CSC data, each of the two forms of the row pass (one warp reduction per
+ * tie-group end, or lane scans per tile for warps that hold many ends),
+ * every candidate from the same cold start; run the path with the fastest,
+ * and keep the choice in the workspace for later calls with the same shape
  * (n, p, number of fits, layout, precision). */
 #define SURV_FLAG_CV_TUNE 4
 /* cox_fit only (CSC data, SURV_PREC_F32C): the sparse-numerator form, not
@@ -345,6 +347,10 @@ typedef struct surv_cv_info {
   int32_t fits_converged;        /* fits that met the tolerance                      */
   int32_t graph_replays;         /* replays of the batched sweep graph               */
   int32_t ctas_per_fit;          /* CTAs each fit runs on in the batched kernels     */
+  int32_t row_pass_form;         /* CSC row pass: 1 one warp reduction per group end, */
+                                 /* 2 lane scans per tile (many ends per warp);      */
+                                 /* 0 for dense X                                    */
+  int32_t reserved;              /* 0                                                */
   int64_t kernel_launches;       /* CUDA kernels launched (graph nodes counted)      */
   int64_t n_groups;              /* tie groups K of the whole data                   */
   int64_t coordinate_passes;     /* risk-set passes summed over fits                 */

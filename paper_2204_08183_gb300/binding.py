@@ -85,7 +85,7 @@ class surv_fit_info(C.Structure):
 class surv_cv_info(C.Structure):
     _fields_ = [("nfits", C.c_int32), ("best_lambda", C.c_int32), ("max_sweeps_used", C.c_int32),
                 ("fits_converged", C.c_int32), ("graph_replays", C.c_int32), ("ctas_per_fit", C.c_int32),
-                ("kernel_launches", C.c_int64), ("n_groups", C.c_int64), ("coordinate_passes", C.c_int64),
+                ("row_pass_form", C.c_int32), ("reserved", C.c_int32), ("kernel_launches", C.c_int64), ("n_groups", C.c_int64), ("coordinate_passes", C.c_int64),
                 ("eta_updates", C.c_int64), ("ccd_kernel_ms", C.c_double), ("heldout_ms", C.c_double)]
 
     def as_dict(self):

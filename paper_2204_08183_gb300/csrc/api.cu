@@ -759,8 +759,11 @@ int cv_impl(const surv_data* d, const int8_t* fold_id, int nfolds, const double*
   const int64_t tkey[6] = {n, p, (int64_t)F, (int64_t)layout * 2 + prec, (int64_t)d->dtype,
                            d->layout == SURV_CSC ? (int64_t)-1 : (int64_t)0};
   int G = ctas_per_fit > 0 ? std::min(ctas_per_fit, Gmax) : cv_ctas_default(F, Gmax, max_by_rows);
-  if (ctas_per_fit == 0 && !tune && ws->cv_tuned_ctas > 0 && std::memcmp(ws->cv_tune_key, tkey, sizeof(tkey)) == 0)
+  int form = 0;  // row-pass form: 0 by the ends per warp
+  if (ctas_per_fit == 0 && !tune && ws->cv_tuned_ctas > 0 && std::memcmp(ws->cv_tune_key, tkey, sizeof(tkey)) == 0) {
     G = ws->cv_tuned_ctas;
+    form = ws->cv_tuned_form;
+  }
   std::vector<int> cands;
   if (tune) {
     for (int g : {G / 2, G, 2 * G, 3 * G})
@@ -845,7 +848,7 @@ int cv_impl(const surv_data* d, const int8_t* fold_id, int nfolds, const double*
   // Grid tables, per-fit parameters and a cold start for G CTAs per fit;
   // *P0 receives the launch parameters (fit 0's, with the table of all fits).
   std::vector<CcdParams> fits_h(F);
-  auto setup = [&](int Gc, CcdParams* P0) -> int {
+  auto setup = [&](int Gc, int form_c, CcdParams* P0) -> int {
     const int32_t nwarps = Gc * wpc;
     const int32_t wpw = (int32_t)((nwords + nwarps - 1) / nwarps);
     const int64_t rows_per_warp = (int64_t)wpw * 32;
@@ -865,6 +868,7 @@ int cv_impl(const surv_data* d, const int8_t* fold_id, int nfolds, const double*
     CUDA_TRY(cudaMemsetAsync(&cvc->done, 0, sizeof(unsigned), s));
     CcdParams P;
     std::memset(&P, 0, sizeof(P));
+    P.pass_form = form_c;
     P.n = n;
     P.ld = stg.ld;
     P.p = (int32_t)p;
@@ -919,24 +923,31 @@ int cv_impl(const surv_data* d, const int8_t* fold_id, int nfolds, const double*
   const int lmode = layout == SURV_CSC ? 0 : 1;
   CcdParams P0;
   if (tune) {
-    // one full sweep of every candidate from the same cold start
+    // one full sweep of every candidate (CTAs per fit x the two forms of the
+    // CSC row pass: one reduction per group end, or lane scans per tile)
+    // from the same cold start
     float best_ms = 0.f;
-    int best_g = G;
-    for (int g : cands) {
-      if ((rc = setup(g, &P0))) return rc;
-      float ms = 0.f;
-      CUDA_TRY(survgpu::time_one_sweep(SURV_COX, lmode, prec, P0, s, &ms));
-      launches += 2 * p;
-      if (best_ms == 0.f || ms < best_ms) {
-        best_ms = ms;
-        best_g = g;
+    int best_g = G, best_form = 0;
+    const std::vector<int> forms = layout == SURV_CSC ? std::vector<int>{1, 2} : std::vector<int>{0};
+    for (int g : cands)
+      for (int fm : forms) {
+        if ((rc = setup(g, fm, &P0))) return rc;
+        float ms = 0.f;
+        CUDA_TRY(survgpu::time_one_sweep(SURV_COX, lmode, prec, P0, s, &ms));
+        launches += 2 * p;
+        if (best_ms == 0.f || ms < best_ms) {
+          best_ms = ms;
+          best_g = g;
+          best_form = fm;
+        }
       }
-    }
     G = best_g;
+    form = best_form;
     ws->cv_tuned_ctas = G;
+    ws->cv_tuned_form = form;
     std::memcpy(ws->cv_tune_key, tkey, sizeof(tkey));
   }
-  if ((rc = setup(G, &P0))) return rc;
+  if ((rc = setup(G, form, &P0))) return rc;
 
   struct Events {
     cudaEvent_t a = nullptr, b = nullptr, c = nullptr;
@@ -993,6 +1004,7 @@ int cv_impl(const surv_data* d, const int8_t* fold_id, int nfolds, const double*
     info->fits_converged = conv;
     info->graph_replays = replays;
     info->ctas_per_fit = G;
+    info->row_pass_form = layout == SURV_CSC ? (form == 2 || (form == 0 && (int64_t)K >= 2 * (int64_t)G * wpc) ? 2 : 1) : 0;
     info->kernel_launches = launches;
     info->n_groups = K;
     info->coordinate_passes = passes;

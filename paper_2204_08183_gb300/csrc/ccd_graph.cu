@@ -658,7 +658,7 @@ cudaError_t capture_sweep(const CcdParams& P, bool pdl, cudaStream_t cs, cudaGra
   auto kp = k_pass<MODEL, LAYOUT, T, false, false>;
   auto kt = k_trans<MODEL, LAYOUT, T, false>;
   if constexpr (MODEL == 0) {
-    const bool multi = (int64_t)P.K >= 2 * (int64_t)P.nwarps;
+    const bool multi = P.pass_form == 2 || (P.pass_form == 0 && (int64_t)P.K >= 2 * (int64_t)P.nwarps);
     if (P.nfit > 0) {
       kp = multi ? k_pass<MODEL, LAYOUT, T, true, true> : k_pass<MODEL, LAYOUT, T, true, false>;
       kt = k_trans<MODEL, LAYOUT, T, true>;

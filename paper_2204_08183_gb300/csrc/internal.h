@@ -66,6 +66,8 @@ struct CcdParams {
   int32_t single_j;      // >= 0: evaluate coordinate single_j once and stop
   int32_t withhold_cta;  // test knob: this CTA never publishes (-1 = off)
   int32_t no_pdl;        // graph schedules: capture without programmatic dependent launch
+  int32_t pass_form;     // Cox CSC row pass: 0 by the ends per warp, 1 one reduction per end,
+                         //   2 the many-ends form (lane scans per tile)
   uint64_t timeout_ns;   // bound on every grid-exchange wait
 
   // per-coordinate kernel pair only (null for the persistent kernel)

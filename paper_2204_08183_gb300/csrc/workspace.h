@@ -40,6 +40,7 @@ struct surv_workspace {
   // CTAs per fit chosen by the cross-validation tuner, and the shape it was
   // tuned for (n, p, fits, layout * 2 + precision, dtype, layout tag)
   int32_t cv_tuned_ctas = 0;
+  int32_t cv_tuned_form = 0;     // and the form of the row pass (CcdParams::pass_form)
   int64_t cv_tune_key[6] = {0, 0, 0, 0, 0, 0};
 };
 

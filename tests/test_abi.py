@@ -61,6 +61,7 @@ int main(void) {
   printf("surv_cv_info %zu\n", sizeof(surv_cv_info));
   F(surv_cv_info, nfits); F(surv_cv_info, best_lambda); F(surv_cv_info, max_sweeps_used);
   F(surv_cv_info, fits_converged); F(surv_cv_info, graph_replays); F(surv_cv_info, ctas_per_fit);
+  F(surv_cv_info, row_pass_form); F(surv_cv_info, reserved);
   F(surv_cv_info, kernel_launches); F(surv_cv_info, n_groups); F(surv_cv_info, coordinate_passes);
   F(surv_cv_info, eta_updates); F(surv_cv_info, ccd_kernel_ms);
   F(surv_cv_info, heldout_ms);
