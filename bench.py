@@ -164,6 +164,77 @@ def oracle_sample(d, lam, n_coords):
     return 1.0 / (per_pass * (d["p"] + 1)), dt, passes
 
 
+def _oracle_core(folder, col, n, lam, barrier, results):
+    """One process of the all-cores oracle timing: a one-sweep fit of column
+    ``col`` alone (3 risk-set passes at full N), started with the others."""
+    import scipy.sparse
+    import oracle
+    t = np.load(os.path.join(folder, "time.npy"))
+    s = np.load(os.path.join(folder, "status.npy"))
+    ri = np.load(os.path.join(folder, "ri%d.npy" % col))
+    X = scipy.sparse.csc_matrix((np.ones(len(ri)), ri, np.array([0, len(ri)])), shape=(n, 1))
+    m = min(n, 20000)  # warm-up on the first rows: one-time costs stay out of the timing
+    oracle.ccd_fit("cox", t[:m], s[:m], X[:m], "l1", lam * m / n, tol=0.0, max_sweeps=1)
+    barrier.wait()
+    t0 = time.perf_counter()
+    oracle.ccd_fit("cox", t, s, X, "l1", lam, tol=0.0, max_sweeps=1)
+    results.put(time.perf_counter() - t0)
+
+
+def oracle_sample_all_cores(d, lam):
+    """The same oracle on every host core at once: one process per core, each
+    a one-sweep fit of its own column (3 risk-set passes at full N), released
+    together by a barrier.  Passes per second = all the processes' passes /
+    the slowest process's time; sweeps/s = that / (p + 1).  Independent passes
+    side by side are the most a host implementation of the same passes could
+    gain from the cores (the passes of one cyclic sweep are sequential).
+    Processes are spawned (this process already holds a CUDA context)."""
+    import multiprocessing as mp
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    ctx = mp.get_context("spawn")
+    with tempfile.TemporaryDirectory() as folder:
+        np.save(os.path.join(folder, "time.npy"), d["time"])
+        np.save(os.path.join(folder, "status.npy"), d["status"])
+        cp = d["col_ptr"]
+        for c in range(cores):
+            j = c % d["p"]
+            np.save(os.path.join(folder, "ri%d.npy" % c), d["row_idx"][cp[j]:cp[j + 1]])
+        barrier = ctx.Barrier(cores)
+        results = ctx.Queue()
+        procs = [ctx.Process(target=_oracle_core, args=(folder, c, d["n"], lam, barrier, results))
+                 for c in range(cores)]
+        # one thread per process (the children read these when numpy loads)
+        saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for k in saved:
+            os.environ[k] = "1"
+        try:
+            for p_ in procs:
+                p_.start()
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        import queue
+        times = []
+        deadline = time.time() + 600
+        while len(times) < cores:
+            try:
+                times.append(results.get(timeout=2))
+            except queue.Empty:
+                if any(p_.exitcode not in (None, 0) for p_ in procs) or time.time() > deadline:
+                    for p_ in procs:
+                        if p_.is_alive():
+                            p_.kill()
+                    raise RuntimeError("all-cores oracle timing: a worker process failed")
+        for p_ in procs:
+            p_.join(timeout=60)
+    passes = 3 * cores
+    per_pass = max(times) / passes
+    return 1.0 / (per_pass * (d["p"] + 1)), max(times), passes, cores
+
+
 # --------------------------------------------------------------- GPU arm
 def run_gpu(args, rank, world):
     import torch
@@ -370,6 +441,12 @@ def run_gpu(args, rank, world):
                                "sample": "oracle.ccd_fit, one sweep over the first 6 of 100 columns at "
                                          "N=1e7 (%d risk-set passes, %.1f s); sweeps/s = 1/(time per pass * "
                                          "(p+1))" % (npass, dt)}
+        sps_all, dt_all, npass_all, cores = oracle_sample_all_cores(d, lam)
+        out["cpu_baseline_all_cores"] = {
+            "value": round(sps_all, 5), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "oracle.ccd_fit on every host core at once: %d processes, each a one-sweep fit of its own "
+                      "column at N=1e7 (%d risk-set passes in all, slowest process %.1f s); sweeps/s = "
+                      "passes / slowest time / (p+1), independent passes side by side" % (cores, npass_all, dt_all)}
     out["beta_nonzero"] = int((beta_final != 0).sum())
     return out
 
