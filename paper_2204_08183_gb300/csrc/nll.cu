@@ -25,6 +25,7 @@
 #include <cstring>
 
 #include "common.cuh"
+#include "tc.cuh"
 #include "survgpu.h"
 #include "workspace.h"
 
@@ -33,8 +34,6 @@ namespace {
 
 constexpr int kNllThreads = 512;   // scan kernels: two CTAs of 16 warps per SM
 constexpr int kNllMaxCols = 64;    // two columns per lane
-constexpr int kRowsAhead = 8;      // rows whose loads a warp of the forward scan keeps in flight
-constexpr int kGradAhead = 4;      // the same for the backward rows (more registers a row)
 
 // B (p x C, row-major FP32) -> Bcat^T (2 Cp rows of ld bf16): row c < C holds
 // hi(B[:, c]), row Cp + c holds lo(B[:, c]) = bf16(B - hi); every other entry
@@ -77,15 +76,81 @@ __device__ __forceinline__ void load_pair(const float* y, int C, int c0, bool ha
   }
 }
 
+// Per-warp staging of eta rows in shared memory by 1-D bulk copies (TMA):
+// kStages slots of kStRows rows (8 C floats: a multiple of 16 bytes, and
+// every stage starts on a 16-byte boundary because warp row ranges start at
+// multiples of 32 rows), one mbarrier each.  Stage s (rows r_lo + 8 s ..)
+// goes to slot s % kStages; lane 0 issues the copies, kStages ahead of the
+// stage the warp reads, and every lane waits (bounded) on the slot's
+// barrier.  Nothing of eta passes through registers before it is used, so
+// three stages (6 KB a warp for 64 columns) keep the memory system busy.
+constexpr int kStRows = 8;
+constexpr int kStages = 3;
+constexpr uint64_t kStageWaitNs = 2000000000ull;
+struct WarpStage {
+  float* buf;          // [kStages][kStRows * C]
+  uint64_t* bar;       // [kStages]
+  const float* src;    // eta + r_lo * C
+  int C;
+  __device__ __forceinline__ void issue(int64_t s) const {
+    const int slot = (int)(s % kStages);
+    const uint32_t bytes = (uint32_t)(kStRows * C * 4);
+    tc::mbar_arrive_expect_tx(bar + slot, bytes);
+    tc::bulk_load(buf + (size_t)slot * kStRows * C, src + (size_t)s * kStRows * C, bytes, bar + slot);
+  }
+  __device__ __forceinline__ bool wait(int64_t s) const {
+    return tc::mbar_wait(bar + (int)(s % kStages), (uint32_t)((s / kStages) & 1), kStageWaitNs);
+  }
+  // columns c0, c0 + 1 of row u of stage s
+  __device__ __forceinline__ void pair(int64_t s, int u, int c0, bool has0, bool has1, float& v0, float& v1) const {
+    const float* r = buf + ((size_t)(s % kStages) * kStRows + u) * C;
+    if (has1 && (C & 1) == 0) {
+      const float2 h = *reinterpret_cast<const float2*>(r + c0);
+      v0 = h.x;
+      v1 = h.y;
+    } else {
+      v0 = has0 ? r[c0] : 0.f;
+      v1 = has1 ? r[c0 + 1] : 0.f;
+    }
+  }
+};
+// Shared memory of the staged scan kernels: kStages stages of every warp.
+size_t stage_smem(int C) { return sizeof(float) * (size_t)(kNllThreads / 32) * kStages * kStRows * C; }
+
+// status of rows r0 .. r0 + 7 packed in two words (one 8-byte broadcast load
+// when the rows are whole and the address allows it)
+__device__ __forceinline__ uint2 load_status8(const int8_t* status, int64_t r0, int64_t r_hi) {
+  if (r0 + 8 <= r_hi && ((reinterpret_cast<uintptr_t>(status + r0)) & 7) == 0)
+    return __ldg(reinterpret_cast<const uint2*>(status + r0));
+  uint32_t w[2] = {0u, 0u};
+#pragma unroll
+  for (int b = 0; b < 8; ++b)
+    if (r0 + b < r_hi) w[b >> 2] |= (uint32_t)(uint8_t)status[r0 + b] << (8 * (b & 3));
+  return make_uint2(w[0], w[1]);
+}
+__device__ __forceinline__ int status_at(uint2 w, int u) {
+  return (int)(int8_t)(((u < 4 ? w.x : w.y) >> (8 * (u & 3))) & 0xFFu);
+}
+
+// Waits (bounded) for the copies a warp issued and has not read: before a
+// CTA that gave up on one of them exits.
+__device__ __forceinline__ void drain_stages(const WarpStage& ws, int64_t s, int64_t nfull) {
+  for (int64_t q = s; q < nfull && q < s + kStages; ++q) ws.wait(q);
+}
+
 // Forward scan.  Warp gw owns rows [gw * rpw, (gw + 1) * rpw); lane l owns
-// the adjacent columns 2l and 2l + 1.  Outputs: rec[k][c] (warp-relative prefix of e at
-// group end k, float-float), wt[gw][c] and wd[gw][c] (the warp's sums of e
-// and of delta * eta).
+// the adjacent columns 2l and 2l + 1.  Outputs: rec[k][c] (warp-relative
+// prefix of e at group end k, float-float), wt[gw][c] and wd[gw][c] (the
+// warp's sums of e and of delta * eta).  Whole stages of 8 rows come through
+// shared memory (bulk copies); the last rows of a warp (fewer than 8) are
+// loaded directly.  A stage wait that expires sets *err.
 __global__ void __launch_bounds__(kNllThreads, 2) k_nll_scan(const float* eta, int64_t n, int C, const int8_t* status,
                                                           const int32_t* gend, const int32_t* wk0, int64_t rpw,
-                                                          float2* rec, float2* wt, float2* wd) {
-  const int lane = threadIdx.x & 31;
-  const int gw = blockIdx.x * (kNllThreads / 32) + (threadIdx.x >> 5);
+                                                          float2* rec, float2* wt, float2* wd, unsigned* err) {
+  extern __shared__ __align__(128) float s_stage[];
+  __shared__ __align__(8) uint64_t s_bar[kNllThreads / 32][kStages];
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  const int gw = blockIdx.x * (kNllThreads / 32) + wl;
   const int64_t r_lo = min((int64_t)gw * rpw, n), r_hi = min(r_lo + rpw, n);
   const int c0 = 2 * lane;
   const bool has0 = c0 < C, has1 = c0 + 1 < C;
@@ -93,26 +158,17 @@ __global__ void __launch_bounds__(kNllThreads, 2) k_nll_scan(const float* eta, i
   int kn = wk0[gw];
   const int k_hi = wk0[gw + 1];
   int64_t next_end = kn < k_hi ? (int64_t)gend[kn] : LLONG_MAX;
-  for (int64_t r0 = r_lo; r0 < r_hi; r0 += kRowsAhead) {
-    float v0[kRowsAhead], v1[kRowsAhead];
-    int8_t st[kRowsAhead];
-#pragma unroll
-    for (int u = 0; u < kRowsAhead; ++u) {
-      const int64_t r = r0 + u;
-      const bool in = r < r_hi;
-      v0[u] = 0.f;
-      v1[u] = 0.f;
-      if (in) load_pair(eta + r * C, C, c0, has0, has1, v0[u], v1[u]);
-      st[u] = in ? status[r] : (int8_t)0;
-    }
+  // rows r0 .. r0 + nr - 1 (nr <= 8) with their eta values and status
+  auto rows = [&](int64_t r0, int nr, const float (&v0)[kStRows], const float (&v1)[kStRows], uint2 st) {
     float p0 = 0.f, p1 = 0.f, q0 = 0.f, q1 = 0.f;
 #pragma unroll
-    for (int u = 0; u < kRowsAhead; ++u) {
+    for (int u = 0; u < kStRows; ++u) {
+      if (u >= nr) break;
       const int64_t r = r0 + u;
       const float e0 = has0 ? expf(v0[u]) : 0.f, e1 = has1 ? expf(v1[u]) : 0.f;
       p0 += e0;
       p1 += e1;
-      if (st[u] == 1) {
+      if (status_at(st, u) == 1) {
         q0 += v0[u];
         q1 += v1[u];
       }
@@ -128,6 +184,46 @@ __global__ void __launch_bounds__(kNllThreads, 2) k_nll_scan(const float* eta, i
     acc1 = ff_add_f(acc1, p1);
     dl0 = ff_add_f(dl0, q0);
     dl1 = ff_add_f(dl1, q1);
+  };
+  const WarpStage ws{s_stage + (size_t)wl * kStages * kStRows * C, s_bar[wl], eta + (size_t)r_lo * C, C};
+  const int64_t nfull = (r_hi - r_lo) / kStRows;
+  if (lane == 0) {
+    for (int q = 0; q < kStages; ++q) tc::mbar_init(&s_bar[wl][q], 1);
+    tc::mbar_fence_init();
+    for (int64_t q = 0; q < nfull && q < kStages; ++q) ws.issue(q);
+  }
+  __syncwarp();
+  uint2 stq[kStages];  // status of the stages in flight
+#pragma unroll
+  for (int q = 0; q < kStages; ++q) stq[q] = load_status8(status, r_lo + (int64_t)q * kStRows, r_hi);
+  for (int64_t s = 0; s < nfull; ++s) {
+    if (!__all_sync(0xffffffffu, ws.wait(s))) {
+      if (lane == 0) atomicOr(err, 1u);
+      drain_stages(ws, s + 1, nfull);
+      return;
+    }
+    float v0[kStRows], v1[kStRows];
+#pragma unroll
+    for (int u = 0; u < kStRows; ++u) ws.pair(s, u, c0, has0, has1, v0[u], v1[u]);
+    const uint2 st = stq[0];
+#pragma unroll
+    for (int q = 0; q + 1 < kStages; ++q) stq[q] = stq[q + 1];
+    stq[kStages - 1] = load_status8(status, r_lo + (s + kStages) * kStRows, r_hi);
+    rows(r_lo + s * kStRows, kStRows, v0, v1, st);
+    tc::fence_proxy_async();  // this lane's reads of the slot before the copy that refills it
+    __syncwarp();
+    if (lane == 0 && s + kStages < nfull) ws.issue(s + kStages);
+  }
+  const int64_t rt = r_lo + nfull * kStRows;
+  if (rt < r_hi) {
+    float v0[kStRows], v1[kStRows];
+#pragma unroll
+    for (int u = 0; u < kStRows; ++u) {
+      v0[u] = 0.f;
+      v1[u] = 0.f;
+      if (rt + u < r_hi) load_pair(eta + (rt + u) * C, C, c0, has0, has1, v0[u], v1[u]);
+    }
+    rows(rt, (int)(r_hi - rt), v0, v1, load_status8(status, rt, r_hi));
   }
   if (has0) {
     wt[(size_t)gw * C + c0] = make_float2(acc0.hi, acc0.lo);
@@ -240,13 +336,16 @@ __global__ void __launch_bounds__(256) k_nll_lambda(const double* den, const int
 
 // Backward per row: G_ic = g_c (e_ic Lambda_c(group of i) - delta_i), written
 // as bf16 in the layout of Bcat: row i holds 2 Cp values, hi(G_ic) at c,
-// lo(G_ic) = bf16(G_ic - hi) at Cp + c, zeros in the padding columns.
+// lo(G_ic) = bf16(G_ic - hi) at Cp + c, zeros in the padding columns.  eta
+// comes through shared memory in stages of 8 rows as in the forward scan.
 __global__ void __launch_bounds__(kNllThreads, 2) k_nll_grad(const float* eta, int64_t n, int C, int Cp,
                                                           const int8_t* status, const int32_t* gend,
                                                           const int32_t* wk0, int64_t rpw, const float* lam,
-                                                          const double* gout, __nv_bfloat16* Gcat) {
-  const int lane = threadIdx.x & 31;
-  const int gw = blockIdx.x * (kNllThreads / 32) + (threadIdx.x >> 5);
+                                                          const double* gout, __nv_bfloat16* Gcat, unsigned* err) {
+  extern __shared__ __align__(128) float s_stage[];
+  __shared__ __align__(8) uint64_t s_bar[kNllThreads / 32][kStages];
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  const int gw = blockIdx.x * (kNllThreads / 32) + wl;
   const int64_t r_lo = min((int64_t)gw * rpw, n), r_hi = min(r_lo + rpw, n);
   const int NB = 2 * Cp;
   const int c0 = 2 * lane;
@@ -262,28 +361,17 @@ __global__ void __launch_bounds__(kNllThreads, 2) k_nll_grad(const float* eta, i
   };
   int64_t cur_end = (int64_t)gend[kn];  // every row < n lies in some group (the last row ends one)
   load_lam();
-  for (int64_t r0 = r_lo; r0 < r_hi; r0 += kGradAhead) {
-    float v0[kGradAhead], v1[kGradAhead];
-    int8_t st[kGradAhead];
+  auto rows = [&](int64_t r0, int nr, const float (&v0)[kStRows], const float (&v1)[kStRows], uint2 st) {
 #pragma unroll
-    for (int u = 0; u < kGradAhead; ++u) {
+    for (int u = 0; u < kStRows; ++u) {
+      if (u >= nr) break;
       const int64_t r = r0 + u;
-      const bool in = r < r_hi;
-      v0[u] = 0.f;
-      v1[u] = 0.f;
-      if (in) load_pair(eta + r * C, C, c0, has0, has1, v0[u], v1[u]);
-      st[u] = in ? status[r] : (int8_t)0;
-    }
-#pragma unroll
-    for (int u = 0; u < kGradAhead; ++u) {
-      const int64_t r = r0 + u;
-      if (r >= r_hi) break;
       if (r > cur_end) {  // past the end of the current group
         ++kn;
         cur_end = (int64_t)gend[kn];
         load_lam();
       }
-      const float d = st[u] == 1 ? 1.f : 0.f;
+      const float d = status_at(st, u) == 1 ? 1.f : 0.f;
       __nv_bfloat16* g = Gcat + r * NB;
       const float x0 = has0 ? g0 * (expf(v0[u]) * l0 - d) : 0.f;
       const float x1 = has1 ? g1 * (expf(v1[u]) * l1 - d) : 0.f;
@@ -295,6 +383,46 @@ __global__ void __launch_bounds__(kNllThreads, 2) k_nll_grad(const float* eta, i
         *reinterpret_cast<__nv_bfloat162*>(g + Cp + c0) = __halves2bfloat162(m0, m1);
       }
     }
+  };
+  const WarpStage ws{s_stage + (size_t)wl * kStages * kStRows * C, s_bar[wl], eta + (size_t)r_lo * C, C};
+  const int64_t nfull = (r_hi - r_lo) / kStRows;
+  if (lane == 0) {
+    for (int q = 0; q < kStages; ++q) tc::mbar_init(&s_bar[wl][q], 1);
+    tc::mbar_fence_init();
+    for (int64_t q = 0; q < nfull && q < kStages; ++q) ws.issue(q);
+  }
+  __syncwarp();
+  uint2 stq[kStages];
+#pragma unroll
+  for (int q = 0; q < kStages; ++q) stq[q] = load_status8(status, r_lo + (int64_t)q * kStRows, r_hi);
+  for (int64_t s = 0; s < nfull; ++s) {
+    if (!__all_sync(0xffffffffu, ws.wait(s))) {
+      if (lane == 0) atomicOr(err, 1u);
+      drain_stages(ws, s + 1, nfull);
+      return;
+    }
+    float v0[kStRows], v1[kStRows];
+#pragma unroll
+    for (int u = 0; u < kStRows; ++u) ws.pair(s, u, c0, has0, has1, v0[u], v1[u]);
+    const uint2 st = stq[0];
+#pragma unroll
+    for (int q = 0; q + 1 < kStages; ++q) stq[q] = stq[q + 1];
+    stq[kStages - 1] = load_status8(status, r_lo + (s + kStages) * kStRows, r_hi);
+    tc::fence_proxy_async();  // this lane's reads of the slot before the copy that refills it
+    __syncwarp();
+    if (lane == 0 && s + kStages < nfull) ws.issue(s + kStages);
+    rows(r_lo + s * kStRows, kStRows, v0, v1, st);
+  }
+  const int64_t rt = r_lo + nfull * kStRows;
+  if (rt < r_hi) {
+    float v0[kStRows], v1[kStRows];
+#pragma unroll
+    for (int u = 0; u < kStRows; ++u) {
+      v0[u] = 0.f;
+      v1[u] = 0.f;
+      if (rt + u < r_hi) load_pair(eta + (rt + u) * C, C, c0, has0, has1, v0[u], v1[u]);
+    }
+    rows(rt, (int)(r_hi - rt), v0, v1, load_status8(status, rt, r_hi));
   }
 }
 
@@ -442,9 +570,11 @@ int cox_nll_forward(const surv_nll_data* d, const float* B, double* nll, void* s
   NLL_TRY(ws_ensure(ws, W::NLL_WT, 2 * sizeof(float2) * (size_t)nwarps * C, &wt));
   NLL_TRY(ws_ensure(ws, W::NLL_DEN, sizeof(double) * (size_t)K * C, &den));
   float2* wt2 = static_cast<float2*>(wt);
-  k_nll_scan<<<G, kNllThreads, 0, s>>>(static_cast<const float*>(Y), n, C, status, static_cast<int32_t*>(gend),
-                                       static_cast<int32_t*>(wk0), rpw, static_cast<float2*>(rec), wt2,
-                                       wt2 + (size_t)nwarps * C);
+  const size_t ssm = stage_smem(C);
+  NLL_TRY(cuda_err(cudaFuncSetAttribute(k_nll_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm), "smem"));
+  k_nll_scan<<<G, kNllThreads, ssm, s>>>(static_cast<const float*>(Y), n, C, status, static_cast<int32_t*>(gend),
+                                         static_cast<int32_t*>(wk0), rpw, static_cast<float2*>(rec), wt2,
+                                         wt2 + (size_t)nwarps * C, static_cast<unsigned*>(errw));
   NLL_TRY(cuda_err(cudaGetLastError(), "scan"));
   const size_t smem = sizeof(float2) * (size_t)nwarps;
   if (smem > 48 * 1024)
@@ -499,9 +629,12 @@ int cox_nll_backward(const surv_nll_data* d, const double* grad_nll, float* grad
   const int32_t* wk0 = static_cast<const int32_t*>(ws->bufs[W::NLL_WK0].p);
   k_nll_lambda<<<C, 256, 0, s>>>(den, dk, K, C, static_cast<float*>(lam));
   NLL_TRY(cuda_err(cudaGetLastError(), "lambda"));
-  k_nll_grad<<<G, kNllThreads, 0, s>>>(static_cast<const float*>(ws->bufs[W::NLL_Y].p), n, C, Cp,
-                                       static_cast<const int8_t*>(d->status), gend, wk0, rpw,
-                                       static_cast<float*>(lam), grad_nll, static_cast<__nv_bfloat16*>(G2));
+  const size_t ssm = stage_smem(C);
+  NLL_TRY(cuda_err(cudaFuncSetAttribute(k_nll_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm), "smem"));
+  k_nll_grad<<<G, kNllThreads, ssm, s>>>(static_cast<const float*>(ws->bufs[W::NLL_Y].p), n, C, Cp,
+                                         static_cast<const int8_t*>(d->status), gend, wk0, rpw,
+                                         static_cast<float*>(lam), grad_nll, static_cast<__nv_bfloat16*>(G2),
+                                         static_cast<unsigned*>(ws->bufs[W::NLL_ERR].p));
   NLL_TRY(cuda_err(cudaGetLastError(), "grad"));
   (void)nwarps;
   // grad_B = X^T [G_hi | G_lo] on the tensor cores, halves and CTA partials
