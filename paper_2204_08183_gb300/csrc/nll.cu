@@ -161,6 +161,18 @@ __global__ void __launch_bounds__(kNllThreads, 2) k_nll_scan(const float* eta, i
   // rows r0 .. r0 + nr - 1 (nr <= 8) with their eta values and status
   auto rows = [&](int64_t r0, int nr, const float (&v0)[kStRows], const float (&v1)[kStRows], uint2 st) {
     float p0 = 0.f, p1 = 0.f, q0 = 0.f, q1 = 0.f;
+    if (nr == kStRows && next_end >= r0 + kStRows) {
+      // no group end among the rows: sums only
+#pragma unroll
+      for (int u = 0; u < kStRows; ++u) {
+        const float dlt = status_at(st, u) == 1 ? 1.f : 0.f;
+        p0 += has0 ? expf(v0[u]) : 0.f;
+        p1 += has1 ? expf(v1[u]) : 0.f;
+        q0 = fmaf(dlt, v0[u], q0);
+        q1 = fmaf(dlt, v1[u], q1);
+      }
+      nr = 0;
+    }
 #pragma unroll
     for (int u = 0; u < kStRows; ++u) {
       if (u >= nr) break;
@@ -362,11 +374,12 @@ __global__ void __launch_bounds__(kNllThreads, 2) k_nll_grad(const float* eta, i
   int64_t cur_end = (int64_t)gend[kn];  // every row < n lies in some group (the last row ends one)
   load_lam();
   auto rows = [&](int64_t r0, int nr, const float (&v0)[kStRows], const float (&v1)[kStRows], uint2 st) {
+    const bool one_group = r0 + nr - 1 <= cur_end;  // every row in the current group
 #pragma unroll
     for (int u = 0; u < kStRows; ++u) {
       if (u >= nr) break;
       const int64_t r = r0 + u;
-      if (r > cur_end) {  // past the end of the current group
+      if (!one_group && r > cur_end) {  // past the end of the current group
         ++kn;
         cur_end = (int64_t)gend[kn];
         load_lam();
