@@ -76,9 +76,18 @@ def parse():
     return ap.parse_args()
 
 
-# Steady-state DRAM bytes per row pass of the headline kernels (ncu capture
-# of the committed k_ipass<4> + k_itrans<4>; None until captured).
-TRAFFIC_IND_ROW_PASS = 18556774
+# Steady-state DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum,
+# ncu --cache-control none, means over 10 launches of each kernel) of the
+# kernels as committed: per row pass of the headline batches (k_ipass<4> +
+# k_itrans<4>), per coordinate of the one-coordinate Cox schedule (k_pass +
+# k_btrans) and of the Fine-Gray fit (k_pass + k_btrans).
+TRAFFIC_IND_ROW_PASS = 18482381
+TRAFFIC_ONE_COORD = 2462618
+TRAFFIC_FG_COORD = 71558144
+# DRAM bytes of one autograd step's four big kernels at N = 2^20, p = 256,
+# 64 columns (k_xb_tc 764.5 MB, k_nll_scan 275.1 MB, k_nll_grad 490.0 MB,
+# k_xtg_tc 805.9 MB; one ncu capture each, cold caches)
+TRAFFIC_AG_STEP_N20 = 2335500000
 
 
 def workload(n, p):
@@ -369,16 +378,16 @@ def run_gpu(args, rank, world):
     if batched:
         roofline.setdefault("traffic", None)
     elif args.schedule == "one" and n == 10_000_000 and p == 100 and not sn:
-        # dram__bytes_read.sum + dram__bytes_write.sum of k_pass + k_trans per
-        # coordinate, steady state (ncu --cache-control none, one pass); see
-        # profiles/k_pass_k_trans_cox_csc_n1e7.md.  e stays in L2 across
-        # coordinates; DRAM sees the column slice and the eta / e writes.
-        roofline["traffic"] = round(0.5 * ((4129792 + 3532032 + 56320 + 3584) + (4101120 + 191232 + 256 + 3328)))
+        # dram__bytes_read.sum + dram__bytes_write.sum of k_pass + k_btrans per
+        # coordinate, steady state; see profiles/k_pass_k_btrans_cox_csc_n1e7.md.
+        # e stays in L2 across coordinates; DRAM sees the column slice and the
+        # eta / e writes.
+        roofline["traffic"] = TRAFFIC_ONE_COORD
         roofline["traffic_note"] = "bytes per coordinate, ncu steady-state capture of the kernels as committed"
     else:
         roofline["traffic"] = None
     roofline["kernel"] = ("ccd_kernel<cox,csc,f32> (persistent, one launch per fit)" if args.schedule == "persistent"
-                          else "k_pass + k_trans <cox,csc,f32>, one pair per coordinate, one graph replay per sweep")
+                          else "k_pass + k_btrans <cox,csc,f32>, one pair per coordinate, one graph replay per sweep")
     if batched:
         bw = args.spec_b
         roofline["kernel"] = (("k_ipass<%d> + k_itrans<%d>" if ind else "k_spass<%d> + k_strans<%d>") % (bw, bw) +
@@ -528,7 +537,14 @@ def run_autograd(args, rank, world):
                       "time_grid": 5000, "censoring": 0.3,
                       "l2": "inputs larger than L2 (X 2 GiB, eta 1 GiB)"},
            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                        "frac": round(achieved / peak, 4), "traffic": None,
+                        "frac": round(achieved / peak, 4),
+                        # DRAM bytes of k_xb_tc + k_nll_scan + k_nll_grad + k_xtg_tc
+                        # in one ncu capture at N = 2^20 (the products and the
+                        # scans move bytes in proportion to N), times 4; see
+                        # profiles/tcgen05_products_cox_nll_p256_c64.md and
+                        # profiles/k_nll_scan_k_nll_grad_n1m_c64.md
+                        "traffic": (TRAFFIC_AG_STEP_N20 * n // (1 << 20)) if p == 256 and C == 64 else None,
+                        "traffic_note": "bytes per step, ncu capture at N=2^20 scaled by N",
                         "algorithmic_bytes_per_step": alg, "implementation_bytes_per_step": moved,
                         "forward_ms": round(fwd_ms, 3), "backward_ms": round(t_max - fwd_ms, 3),
                         "kernel": "tcgen05 products k_xb_tc (X B) and k_xtg_tc (X^T G), TMA + TMEM, "
@@ -674,6 +690,7 @@ def run_cv(args, rank, world):
                       "l2": "inputs larger than L2 (e + eta of 200 fits: 2.4 GB)"},
            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                         "frac": round(achieved / peak, 4), "traffic": None,
+                        "traffic_note": "not a whole-path figure: a capture of early launches (all 200 fits active, most passes streaming e) read 440-540 MB and wrote 56-78 MB a launch; see profiles/k_pass_batched_cv_n1e6.md",
                         "unit_of_work": "one coordinate of one active fit (batched row pass)",
                         "algorithmic_bytes_per_coordinate": round(alg / max(passes, 1)),
                         "coordinate_passes_per_step": passes / len(infos),
@@ -866,7 +883,14 @@ def run_fg(args, rank, world):
                 "passes_per_fit": passes / len(infos), "eta_updates_per_fit": upd / len(infos),
                 "kernel": ("ccd_kernel<fg,dense,f32> (persistent, one launch per fit)"
                            if args.schedule == "persistent" else
-                           "k_pass + k_trans <fg,dense,f32>, one pair per coordinate, one graph replay per sweep")}
+                           "k_pass + k_btrans <fg,dense,f32>, one pair per coordinate, one graph replay per sweep")}
+    if args.schedule == "graph" and n == 5_000_000 and p == 50:
+        # steady-state DRAM bytes per coordinate (see
+        # profiles/k_pass_k_btrans_fg_dense_n5e6.md): below the algorithmic
+        # bytes because the previous coordinate's column (read again for the
+        # eta update) and part of eta / e / W are still in L2
+        roofline["traffic"] = TRAFFIC_FG_COORD
+        roofline["traffic_note"] = "bytes per coordinate, ncu steady-state capture of the kernels as committed"
     out = {"metric": FG_METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 3), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
