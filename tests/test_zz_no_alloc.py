@@ -69,7 +69,7 @@ def test_noalloc_rejects_malformed_col_ptr_on_the_host(lib):
     n = 64
     t = torch.arange(n, 0, -1, dtype=torch.int32).cuda()
     s = torch.ones(n, dtype=torch.int8).cuda()
-    ri = torch.tensor([1, 4, 9, 2, 3, 7, 8, 11], dtype=torch.int32).cuda()
+    ri = torch.tensor([1, 2, 3, 4, 9, 7, 8, 11], dtype=torch.int32).cuda()   # rows increase within each column
     for cp in ([2, 5, 8], [0, 5, 3]):                       # col_ptr[0] != 0; decreasing
         d = binding.SurvData(t, s, col_ptr=torch.tensor(cp, dtype=torch.int64).cuda(), row_idx=ri)
         with pytest.raises(binding.SurvError) as ei:
