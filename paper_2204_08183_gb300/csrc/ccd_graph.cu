@@ -426,7 +426,7 @@ constexpr int kBtNT = 512;
 constexpr int kBtWarps = kBtNT / 32;
 
 template <int MODEL, int LAYOUT, typename T>
-__global__ void __launch_bounds__(kBtNT) k_btrans(const __grid_constant__ CcdParams P, int j) {
+__global__ void __launch_bounds__(kBtNT, 1) k_btrans(const __grid_constant__ CcdParams P, int j) {
   using A = typename AccOf<T>::type;
   constexpr int M = MODEL == 0 ? 3 : 6;
   __shared__ A s_T[kBtNT][M];
