@@ -710,7 +710,7 @@ __global__ void __launch_bounds__(kSpNT, 2) k_ipass(const __grid_constant__ CcdP
 }
 
 template <int B>
-__global__ void __launch_bounds__(kItNT) k_itrans(const __grid_constant__ CcdParams P, int slot) {
+__global__ void __launch_bounds__(kItNT, 1) k_itrans(const __grid_constant__ CcdParams P, int slot) {
   constexpr int R = IpCfg<B>::R, NP = IpCfg<B>::NP, NPP = IpCfg<B>::NPP;
   __shared__ ff s_T[kItNT][R];           // exclusive prefix of the pass CTAs' aggregates (G <= kItNT)
   __shared__ ff s_w[kItWarps][R];        // warp totals of that scan, then their exclusive prefix
