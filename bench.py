@@ -685,7 +685,12 @@ def run_cv(args, rank, world):
                       "ctas_per_fit": infos[-1]["ctas_per_fit"],
                       "row_pass_form": {1: "one warp reduction per group end",
                                         2: "lane scans per tile"}[infos[-1]["row_pass_form"]],
-                      "ctas_source": "autotuned with the row-pass form (one timed sweep per candidate, first warm-up call)"
+                      "tile_form": {0: "4 loads of e per lane a tile, 4 rounds of nonzeros a load",
+                                    1: "2 loads of e per lane a tile, 4 rounds of nonzeros a load",
+                                    2: "4 loads of e per lane a tile, 2 rounds of nonzeros a load"}[
+                          infos[-1]["tile_form"]],
+                      "ctas_source": "autotuned with the row-pass form and tile shape (one timed sweep per "
+                                     "candidate, first warm-up call)"
                       if args.ctas == 0 else "--ctas",
                       "l2": "inputs larger than L2 (e + eta of 200 fits: 2.4 GB)"},
            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",

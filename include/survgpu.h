@@ -131,9 +131,10 @@ typedef struct surv_opts {
 /* cox_cv_path only, with ctas_per_fit = 0: time one sweep of the batched
  * schedule for each of a few CTA-per-fit counts around the default and, for
  * CSC data, each of the two forms of the row pass (one warp reduction per
- * tie-group end, or lane scans per tile for warps that hold many ends),
- * every candidate from the same cold start; run the path with the fastest,
- * and keep the choice in the workspace for later calls with the same shape
+ * tie-group end, or lane scans per tile for warps that hold many ends) and,
+ * in the FP32 mode, three tile shapes (see surv_cv_info.tile_form), every
+ * candidate from the same cold start; run the path with the fastest, and
+ * keep the choice in the workspace for later calls with the same shape
  * (n, p, number of fits, layout, precision). */
 #define SURV_FLAG_CV_TUNE 4
 /* cox_fit only (CSC data, SURV_PREC_F32C): the sparse-numerator form, not
@@ -165,6 +166,12 @@ typedef struct surv_opts {
  * launch (each kernel starts after the previous one has finished), for
  * comparison with the default. */
 #define SURV_FLAG_NO_PDL 64
+/* cox_cv_path only, CSC data in the FP32 mode: run the batched row pass with
+ * tile shape 1 (two 16-byte loads of e per lane a tile) or 2 (two rounds of
+ * 32 nonzeros a load) instead of the tuned or default shape, for comparison
+ * and testing (surv_cv_info.tile_form reports the shape that ran). */
+#define SURV_FLAG_CV_TILE1 256
+#define SURV_FLAG_CV_TILE2 512
 
 /* Fill *opts with defaults: no penalty, FP32-compensated precision,
  * tol 1e-8, max_sweeps 1000, default stream, no workspace. */
@@ -350,7 +357,9 @@ typedef struct surv_cv_info {
   int32_t row_pass_form;         /* CSC row pass: 1 one warp reduction per group end, */
                                  /* 2 lane scans per tile (many ends per warp);      */
                                  /* 0 for dense X                                    */
-  int32_t reserved;              /* 0                                                */
+  int32_t tile_form;             /* CSC FP32 row pass: 0 four 16-byte loads of e per */
+                                 /* lane a tile and 4 rounds of 32 nonzeros a load,  */
+                                 /* 1 two loads, 2 two rounds                        */
   int64_t kernel_launches;       /* CUDA kernels launched (graph nodes counted)      */
   int64_t n_groups;              /* tie groups K of the whole data                   */
   int64_t coordinate_passes;     /* risk-set passes summed over fits                 */

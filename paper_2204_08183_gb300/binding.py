@@ -43,6 +43,8 @@ SURV_FLAG_SPARSE_NUMERATOR = 8
 SURV_FLAG_ONE_COORDINATE = 16
 SURV_FLAG_SPEC_B8 = 32
 SURV_FLAG_NO_PDL = 64
+SURV_FLAG_CV_TILE1 = 256
+SURV_FLAG_CV_TILE2 = 512
 
 # exported symbols, in the order the header declares them
 EXPORTS = ["surv_opts_default", "surv_workspace_create", "surv_workspace_destroy", "surv_sort_desc",
@@ -85,7 +87,7 @@ class surv_fit_info(C.Structure):
 class surv_cv_info(C.Structure):
     _fields_ = [("nfits", C.c_int32), ("best_lambda", C.c_int32), ("max_sweeps_used", C.c_int32),
                 ("fits_converged", C.c_int32), ("graph_replays", C.c_int32), ("ctas_per_fit", C.c_int32),
-                ("row_pass_form", C.c_int32), ("reserved", C.c_int32), ("kernel_launches", C.c_int64), ("n_groups", C.c_int64), ("coordinate_passes", C.c_int64),
+                ("row_pass_form", C.c_int32), ("tile_form", C.c_int32), ("kernel_launches", C.c_int64), ("n_groups", C.c_int64), ("coordinate_passes", C.c_int64),
                 ("eta_updates", C.c_int64), ("ccd_kernel_ms", C.c_double), ("heldout_ms", C.c_double)]
 
     def as_dict(self):

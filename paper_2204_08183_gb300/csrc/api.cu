@@ -715,7 +715,11 @@ int cv_impl(const surv_data* d, const int8_t* fold_id, int nfolds, const double*
   if (ctas_per_fit < 0) { set_error("negative ctas_per_fit"); return SURV_E_INVALID; }
   if (o.penalty < 0 || o.penalty > 2 || o.precision < 0 || o.precision > 1) { set_error("bad penalty/precision"); return SURV_E_INVALID; }
   if (!(o.tol >= 0.0) || o.max_sweeps < 0) { set_error("bad tol/max_sweeps"); return SURV_E_INVALID; }
-  if ((o.flags & ~SURV_FLAG_CV_TUNE) != 0) { set_error("unknown flags for cox_cv_path"); return SURV_E_INVALID; }
+  if ((o.flags & ~(SURV_FLAG_CV_TUNE | SURV_FLAG_CV_TILE1 | SURV_FLAG_CV_TILE2)) != 0 ||
+      (o.flags & SURV_FLAG_CV_TILE1 && o.flags & SURV_FLAG_CV_TILE2)) {
+    set_error("unknown flags for cox_cv_path");
+    return SURV_E_INVALID;
+  }
   const int64_t n = d->n, p = d->p;
   const int F = nfolds * nlambda;
   const int layout = d->layout;
@@ -760,10 +764,15 @@ int cv_impl(const surv_data* d, const int8_t* fold_id, int nfolds, const double*
                            d->layout == SURV_CSC ? (int64_t)-1 : (int64_t)0};
   int G = ctas_per_fit > 0 ? std::min(ctas_per_fit, Gmax) : cv_ctas_default(F, Gmax, max_by_rows);
   int form = 0;  // row-pass form: 0 by the ends per warp
+  int tile = 0;  // tile shape of the CSC FP32 row pass
   if (ctas_per_fit == 0 && !tune && ws->cv_tuned_ctas > 0 && std::memcmp(ws->cv_tune_key, tkey, sizeof(tkey)) == 0) {
     G = ws->cv_tuned_ctas;
     form = ws->cv_tuned_form;
+    tile = ws->cv_tuned_tile;
   }
+  const int tile_forced = (o.flags & SURV_FLAG_CV_TILE1) ? 1 : ((o.flags & SURV_FLAG_CV_TILE2) ? 2 : -1);
+  const bool tile_ok = layout == SURV_CSC && prec == 0;  // the shapes exist for CSC data in the FP32 mode
+  if (tile_forced >= 0) tile = tile_ok ? tile_forced : 0;
   std::vector<int> cands;
   if (tune) {
     for (int g : {G / 2, G, 2 * G, 3 * G})
@@ -848,7 +857,7 @@ int cv_impl(const surv_data* d, const int8_t* fold_id, int nfolds, const double*
   // Grid tables, per-fit parameters and a cold start for G CTAs per fit;
   // *P0 receives the launch parameters (fit 0's, with the table of all fits).
   std::vector<CcdParams> fits_h(F);
-  auto setup = [&](int Gc, int form_c, CcdParams* P0) -> int {
+  auto setup = [&](int Gc, int form_c, int tile_c, CcdParams* P0) -> int {
     const int32_t nwarps = Gc * wpc;
     const int32_t wpw = (int32_t)((nwords + nwarps - 1) / nwarps);
     const int64_t rows_per_warp = (int64_t)wpw * 32;
@@ -869,6 +878,7 @@ int cv_impl(const surv_data* d, const int8_t* fold_id, int nfolds, const double*
     CcdParams P;
     std::memset(&P, 0, sizeof(P));
     P.pass_form = form_c;
+    P.tile_form = tile_c;
     P.n = n;
     P.ld = stg.ld;
     P.p = (int32_t)p;
@@ -923,31 +933,39 @@ int cv_impl(const surv_data* d, const int8_t* fold_id, int nfolds, const double*
   const int lmode = layout == SURV_CSC ? 0 : 1;
   CcdParams P0;
   if (tune) {
-    // one full sweep of every candidate (CTAs per fit x the two forms of the
-    // CSC row pass: one reduction per group end, or lane scans per tile)
-    // from the same cold start
+    // one full sweep of every candidate from the same cold start: CTAs per
+    // fit x, for CSC data, the two forms of the row pass (one reduction per
+    // group end, or lane scans per tile) x, in the FP32 mode, three tile
+    // shapes (the configured one, half the loads of e per lane, half the
+    // rounds of nonzeros per load)
     float best_ms = 0.f;
-    int best_g = G, best_form = 0;
+    int best_g = G, best_form = 0, best_tile = 0;
     const std::vector<int> forms = layout == SURV_CSC ? std::vector<int>{1, 2} : std::vector<int>{0};
+    const std::vector<int> tiles = tile_forced >= 0 ? std::vector<int>{tile}
+                                   : (tile_ok ? std::vector<int>{0, 1, 2} : std::vector<int>{0});
     for (int g : cands)
-      for (int fm : forms) {
-        if ((rc = setup(g, fm, &P0))) return rc;
-        float ms = 0.f;
-        CUDA_TRY(survgpu::time_one_sweep(SURV_COX, lmode, prec, P0, s, &ms));
-        launches += 2 * p;
-        if (best_ms == 0.f || ms < best_ms) {
-          best_ms = ms;
-          best_g = g;
-          best_form = fm;
+      for (int fm : forms)
+        for (int tw : tiles) {
+          if ((rc = setup(g, fm, tw, &P0))) return rc;
+          float ms = 0.f;
+          CUDA_TRY(survgpu::time_one_sweep(SURV_COX, lmode, prec, P0, s, &ms));
+          launches += 2 * p;
+          if (best_ms == 0.f || ms < best_ms) {
+            best_ms = ms;
+            best_g = g;
+            best_form = fm;
+            best_tile = tw;
+          }
         }
-      }
     G = best_g;
     form = best_form;
+    tile = best_tile;
     ws->cv_tuned_ctas = G;
     ws->cv_tuned_form = form;
+    ws->cv_tuned_tile = tile;
     std::memcpy(ws->cv_tune_key, tkey, sizeof(tkey));
   }
-  if ((rc = setup(G, form, &P0))) return rc;
+  if ((rc = setup(G, form, tile, &P0))) return rc;
 
   struct Events {
     cudaEvent_t a = nullptr, b = nullptr, c = nullptr;
@@ -1005,6 +1023,7 @@ int cv_impl(const surv_data* d, const int8_t* fold_id, int nfolds, const double*
     info->graph_replays = replays;
     info->ctas_per_fit = G;
     info->row_pass_form = layout == SURV_CSC ? (form == 2 || (form == 0 && (int64_t)K >= 2 * (int64_t)G * wpc) ? 2 : 1) : 0;
+    info->tile_form = tile;
     info->kernel_launches = launches;
     info->n_groups = K;
     info->coordinate_passes = passes;

@@ -81,7 +81,10 @@ __global__ void k_graph_init(const __grid_constant__ CcdParams P0) {
 
 // MULTI selects the group-end handling for warps that hold many ends (see
 // warp_pass); the host picks it when the tie groups outnumber the warps.
-template <int MODEL, int LAYOUT, typename T, bool BATCH, bool MULTI>
+// TW picks the tile shape: 0 the configured one, 1 half the 16-byte loads of
+// e per lane a tile, 2 half the rounds of nonzeros loaded together (twice
+// the loads spilled at the 64-register cap).
+template <int MODEL, int LAYOUT, typename T, bool BATCH, bool MULTI, int TW = 0>
 __global__ void __launch_bounds__(GCfg<MODEL, LAYOUT>::NT, GCfg<MODEL, LAYOUT>::MINB)
     k_pass(const __grid_constant__ CcdParams P0, int j) {
   using A = typename AccOf<T>::type;
@@ -113,8 +116,10 @@ __global__ void __launch_bounds__(GCfg<MODEL, LAYOUT>::NT, GCfg<MODEL, LAYOUT>::
   // column j's first nonzeros and the warp's group ends do not depend on
   // earlier kernels: load them before waiting for the previous kernel
   using GC = GCfg<MODEL, LAYOUT>;
-  PassPrefetch<T, GC::SR> pf;
-  pass_prefetch<LAYOUT, T, GC::SR>(P, j, gw, pf);
+  constexpr int U = TW == 1 ? (GC::U > 1 ? GC::U / 2 : 1) : GC::U;
+  constexpr int SR = TW == 2 ? GC::SR / 2 : GC::SR;
+  PassPrefetch<T, SR> pf;
+  pass_prefetch<LAYOUT, T, SR>(P, j, gw, pf);
   pdl_wait();
 
   // the step of q (zero before the first coordinate of a fit), read once
@@ -142,8 +147,7 @@ __global__ void __launch_bounds__(GCfg<MODEL, LAYOUT>::NT, GCfg<MODEL, LAYOUT>::
   // ------------------------------------------- step 2 for coordinate j
   A* rec = reinterpret_cast<A*>(P.rec);
   A tot[M];
-  warp_pass<MODEL, LAYOUT, T, GC::U, GC::SR, MULTI>(P, j, row_lo, row_hi, rec, tot, pf, dense, xq,
-                                                    ff{s_delta[0], s_delta[1]});
+  warp_pass<MODEL, LAYOUT, T, U, SR, MULTI>(P, j, row_lo, row_hi, rec, tot, pf, dense, xq, ff{s_delta[0], s_delta[1]});
   pdl_launch_dependents();
   if (lane == 0)
 #pragma unroll
@@ -661,6 +665,11 @@ cudaError_t capture_sweep(const CcdParams& P, bool pdl, cudaStream_t cs, cudaGra
     const bool multi = P.pass_form == 2 || (P.pass_form == 0 && (int64_t)P.K >= 2 * (int64_t)P.nwarps);
     if (P.nfit > 0) {
       kp = multi ? k_pass<MODEL, LAYOUT, T, true, true> : k_pass<MODEL, LAYOUT, T, true, false>;
+      if constexpr (LAYOUT == 0 && sizeof(T) == 4) {
+        // tile shapes the cross-validation tuner may pick
+        if (P.tile_form == 1) kp = multi ? k_pass<MODEL, LAYOUT, T, true, true, 1> : k_pass<MODEL, LAYOUT, T, true, false, 1>;
+        if (P.tile_form == 2) kp = multi ? k_pass<MODEL, LAYOUT, T, true, true, 2> : k_pass<MODEL, LAYOUT, T, true, false, 2>;
+      }
       kt = k_trans<MODEL, LAYOUT, T, true>;
     } else if (multi) {
       kp = k_pass<MODEL, LAYOUT, T, false, true>;

@@ -68,6 +68,8 @@ struct CcdParams {
   int32_t no_pdl;        // graph schedules: capture without programmatic dependent launch
   int32_t pass_form;     // Cox CSC row pass: 0 by the ends per warp, 1 one reduction per end,
                          //   2 the many-ends form (lane scans per tile)
+  int32_t tile_form;     // batched Cox CSC FP32 row pass: 0 four 16-byte loads of e per lane a
+                         //   tile and 4 rounds of nonzeros a load, 1 two loads, 2 two rounds
   uint64_t timeout_ns;   // bound on every grid-exchange wait
 
   // per-coordinate kernel pair only (null for the persistent kernel)

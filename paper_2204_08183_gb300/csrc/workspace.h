@@ -41,6 +41,7 @@ struct surv_workspace {
   // tuned for (n, p, fits, layout * 2 + precision, dtype, layout tag)
   int32_t cv_tuned_ctas = 0;
   int32_t cv_tuned_form = 0;     // and the form of the row pass (CcdParams::pass_form)
+  int32_t cv_tuned_tile = 0;     // and its tile shape (CcdParams::tile_form)
   int64_t cv_tune_key[6] = {0, 0, 0, 0, 0, 0};
 };
 

@@ -61,7 +61,7 @@ int main(void) {
   printf("surv_cv_info %zu\n", sizeof(surv_cv_info));
   F(surv_cv_info, nfits); F(surv_cv_info, best_lambda); F(surv_cv_info, max_sweeps_used);
   F(surv_cv_info, fits_converged); F(surv_cv_info, graph_replays); F(surv_cv_info, ctas_per_fit);
-  F(surv_cv_info, row_pass_form); F(surv_cv_info, reserved);
+  F(surv_cv_info, row_pass_form); F(surv_cv_info, tile_form);
   F(surv_cv_info, kernel_launches); F(surv_cv_info, n_groups); F(surv_cv_info, coordinate_passes);
   F(surv_cv_info, eta_updates); F(surv_cv_info, ccd_kernel_ms);
   F(surv_cv_info, heldout_ms);
@@ -123,7 +123,8 @@ def test_binding_fails_loudly_without_the_library(tmp_path, monkeypatch):
 def test_header_documents_every_flag_the_binding_uses():
     text = open(HEADER).read()
     for name in ("SURV_FLAG_TEST_STALL", "SURV_FLAG_PERSISTENT", "SURV_FLAG_CV_TUNE", "SURV_FLAG_SPARSE_NUMERATOR",
-                 "SURV_FLAG_ONE_COORDINATE", "SURV_FLAG_SPEC_B8", "SURV_FLAG_NO_PDL"):
+                 "SURV_FLAG_ONE_COORDINATE", "SURV_FLAG_SPEC_B8", "SURV_FLAG_NO_PDL",
+                 "SURV_FLAG_CV_TILE1", "SURV_FLAG_CV_TILE2"):
         m = re.search(r"#define %s (\d+)" % name, text)
         assert m and int(m.group(1)) == getattr(binding, name), name
 

@@ -22,10 +22,10 @@ TOL_B = {"f32c": 1e-5, "f64": 1e-9}
 TOL_H = {"f32c": 1e-6, "f64": 1e-10}
 
 
-def _compare(d, fold, nfolds, lambdas, penalty, prec, ctas=0, tol=1e-9):
+def _compare(d, fold, nfolds, lambdas, penalty, prec, ctas=0, tol=1e-9, flags=0):
     sd = survdata(d)
     r = binding.cox_cv_path(sd, fold, nfolds, lambdas, penalty=penalty, precision=prec, tol=tol,
-                            max_sweeps=200, ctas_per_fit=ctas)
+                            max_sweeps=200, ctas_per_fit=ctas, flags=flags)
     info = r["info"]
     assert info["nfits"] == len(lambdas) * nfolds
     assert info["fits_converged"] == info["nfits"]
@@ -49,6 +49,18 @@ def test_cv_path_csc_matches_oracle(lib, prec, ctas):
     lmax = binding.cox_lambda_max(survdata(d))
     lam = synth.lambda_grid(lmax, 4, ratio=1e-2)
     _compare(d, fold, 3, lam, "l1", prec, ctas)
+
+
+@pytest.mark.parametrize("tile", [1, 2])
+@pytest.mark.parametrize("n_times", [20, 300])   # few ends per warp (one reduction an end) / many (lane scans)
+def test_cv_path_tile_shapes_match_oracle(lib, tile, n_times):
+    d = small_csc(3001, 10, seed=31, density=0.3, n_times=n_times)
+    fold = synth.cv_folds(3001, 3, seed=32)
+    lam = synth.lambda_grid(binding.cox_lambda_max(survdata(d)), 4, ratio=1e-2)
+    flag = binding.SURV_FLAG_CV_TILE1 if tile == 1 else binding.SURV_FLAG_CV_TILE2
+    r, _ = _compare(d, fold, 3, lam, "l1", "f32c", ctas=3, flags=flag)
+    assert r["info"]["tile_form"] == tile
+    assert r["info"]["row_pass_form"] == (2 if n_times == 300 else 1)
 
 
 @pytest.mark.parametrize("prec", ["f32c", "f64"])
@@ -80,10 +92,10 @@ def test_cv_tuner_picks_a_candidate_and_is_reused(lib):
     ws = binding.Workspace()
     lam = [50.0, 5.0, 0.5]
     r = binding.cox_cv_path(sd, fold, 5, lam, penalty="l1", tol=1e-9, workspace=ws, flags=binding.SURV_FLAG_CV_TUNE)
-    g, form = r["info"]["ctas_per_fit"], r["info"]["row_pass_form"]
-    assert g >= 1 and form in (1, 2)
+    g, form, tile = r["info"]["ctas_per_fit"], r["info"]["row_pass_form"], r["info"]["tile_form"]
+    assert g >= 1 and form in (1, 2) and tile in (0, 1, 2)
     r2 = binding.cox_cv_path(sd, fold, 5, lam, penalty="l1", tol=1e-9, workspace=ws)
-    assert (r2["info"]["ctas_per_fit"], r2["info"]["row_pass_form"]) == (g, form)
+    assert (r2["info"]["ctas_per_fit"], r2["info"]["row_pass_form"], r2["info"]["tile_form"]) == (g, form, tile)
     np.testing.assert_array_equal(r["beta"], r2["beta"])
     ref = oracle.cv_path(d["time"], d["status"], oracle_X(d), fold, 5, lam, "l1", sweeps=r["sweeps"])
     np.testing.assert_allclose(r["beta"], ref["beta"], rtol=0, atol=TOL_B["f32c"])
