@@ -81,9 +81,9 @@ def parse():
 # kernels as committed: per row pass of the headline batches (k_ipass<4> +
 # k_itrans<4>), per coordinate of the one-coordinate Cox schedule (k_pass +
 # k_btrans) and of the Fine-Gray fit (k_pass + k_btrans).
-TRAFFIC_IND_ROW_PASS = 18482381
-TRAFFIC_ONE_COORD = 2462618
-TRAFFIC_FG_COORD = 71558144
+TRAFFIC_IND_ROW_PASS = 18825933
+TRAFFIC_ONE_COORD = 2435456
+TRAFFIC_FG_COORD = 71040486
 # DRAM bytes of one autograd step's four big kernels at N = 2^20, p = 256,
 # 64 columns (k_xb_tc 764.5 MB, k_nll_scan 275.1 MB, k_nll_grad 490.0 MB,
 # k_xtg_tc 805.9 MB; one ncu capture each, cold caches)
