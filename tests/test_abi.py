@@ -207,6 +207,8 @@ def test_argument_errors_before_any_device_call(libpath):
     assert code(binding.cox_cv_path, good, fold, 0, lam) == E.SURV_E_INVALID
     assert code(binding.cox_cv_path, good, fold, 128, lam) == E.SURV_E_INVALID
     assert code(binding.cox_cv_path, good, fold, 2, lam, ctas_per_fit=-1) == E.SURV_E_INVALID
+    both = binding.SURV_FLAG_CV_TILE1 | binding.SURV_FLAG_CV_TILE2        # two tile shapes at once
+    assert code(binding.cox_cv_path, good, fold, 2, lam, flags=both) == E.SURV_E_INVALID
     assert code(binding.cox_cv_path, good, fold, 2, lam, flags=binding.SURV_FLAG_ONE_COORDINATE) == E.SURV_E_INVALID
     assert code(binding.cox_cv_path, empty, fold, 2, lam) == E.SURV_E_NO_EVENTS
     # lambda_max checks the data first
