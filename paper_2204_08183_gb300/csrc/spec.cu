@@ -523,7 +523,9 @@ struct IpCfg {
   static constexpr int RP = R <= 2 ? 2 : (R <= 4 ? 4 : (R <= 8 ? 8 : (R <= 16 ? 16 : 32)));
   static constexpr int NP = 2 * B + 1;
   static constexpr int NPP = NP <= 2 ? 2 : (NP <= 4 ? 4 : (NP <= 8 ? 8 : (NP <= 16 ? 16 : 32)));
-  static constexpr int SR = B <= 4 ? 2 : 1;  // rounds of 32 nonzeros per column in flight
+  // rounds of 32 nonzeros per column in flight: one (two spilled at the
+  // 64-register cap of two CTAs per SM and measured 2 % slower)
+  static constexpr int SR = 1;
 };
 constexpr int kItNT = 512;   // transform kernel threads
 constexpr int kItWarps = kItNT / 32;
