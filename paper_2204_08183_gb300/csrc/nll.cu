@@ -247,18 +247,24 @@ __global__ void __launch_bounds__(kNllThreads, 2) k_nll_scan(const float* eta, i
   }
 }
 
-// Per column c (one CTA of kFinThreads each): prefix of the warp totals in a
-// fixed order (chunk sums, a two-level block scan, the prefix inside each
-// chunk), den_k = prefix before the end's warp + rec[k][c] (kept for the
-// backward), NLL_c = -sum delta eta + sum_k d_k log den_k (logs and the
-// sums in FP64; many threads, because the FP64 logs dominate).
+// Per column c, S CTAs of kFinThreads each (grid C x S): prefix of the warp
+// totals in a fixed order (chunk sums, a two-level block scan, the prefix
+// inside each chunk; every CTA of the column computes it), den_k = prefix
+// before the end's warp + rec[k][c] (kept for the backward) and d_k log den_k
+// for the ends k = s kFinThreads + tid (stride S kFinThreads): the FP64 logs
+// dominate, so the column's ends are spread over S CTAs.  Each CTA stores its
+// sums in part[c][s]; the column's last CTA (ticket cnt[c], reset after use)
+// adds them in the order s = 0 .. S-1: NLL_c = -sum delta eta + sum_k d_k
+// log den_k.
 constexpr int kFinThreads = 1024;
 __global__ void __launch_bounds__(kFinThreads) k_nll_finish(const float2* rec, const float2* wt, const float2* wd,
                                                           int nwarps, int C, const int32_t* gend, const int32_t* dk,
-                                                          int K, int64_t rpw, double* den, double* nll) {
+                                                          int K, int64_t rpw, double* den, double* part,
+                                                          unsigned* cnt, double* nll) {
   extern __shared__ float2 s_base[];  // [nwarps] exclusive prefix (float-float)
   __shared__ ff s_ws[32];
   __shared__ double s_red[32][2];
+  __shared__ int s_last;
   const int c = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int ch = (nwarps + kFinThreads - 1) / kFinThreads;
@@ -286,9 +292,10 @@ __global__ void __launch_bounds__(kFinThreads) k_nll_finish(const float2* rec, c
     pre = ff_add(pre, ff{v.x, v.y});
   }
   __syncthreads();
-  // the group ends: den in FP64, d log den
+  // the group ends of this CTA: den in FP64, d log den
+  const int S = gridDim.y, sc = blockIdx.y;
   double sl = 0.0, sd = 0.0;
-  for (int k = tid; k < K; k += kFinThreads) {
+  for (int k = sc * kFinThreads + tid; k < K; k += S * kFinThreads) {
     const int q = (int)(gend[k] / rpw);
     const float2 b = s_base[q];
     const float2 r = rec[(size_t)k * C + c];
@@ -297,10 +304,11 @@ __global__ void __launch_bounds__(kFinThreads) k_nll_finish(const float2* rec, c
     den[(size_t)k * C + c] = d;
     if (dk[k] != 0) sl += (double)dk[k] * log(d);
   }
-  for (int q = tid; q < nwarps; q += kFinThreads) {
-    const float2 v = wd[(size_t)q * C + c];
-    sd += (double)v.x + (double)v.y;
-  }
+  if (sc == 0)
+    for (int q = tid; q < nwarps; q += kFinThreads) {
+      const float2 v = wd[(size_t)q * C + c];
+      sd += (double)v.x + (double)v.y;
+    }
   sl = warp_sum(sl);
   sd = warp_sum(sd);
   if (lane == 0) {
@@ -314,35 +322,58 @@ __global__ void __launch_bounds__(kFinThreads) k_nll_finish(const float2* rec, c
       a += s_red[q][0];
       b += s_red[q][1];
     }
+    part[((size_t)c * S + sc) * 2] = a;
+    part[((size_t)c * S + sc) * 2 + 1] = b;
+    __threadfence();
+    s_last = atomicAdd(cnt + c, 1u) == (unsigned)(S - 1);
+  }
+  __syncthreads();
+  if (tid == 0 && s_last) {
+    __threadfence();
+    double a = 0.0, b = 0.0;
+    for (int q = 0; q < S; ++q) {
+      a += __ldcg(part + ((size_t)c * S + q) * 2);
+      b += __ldcg(part + ((size_t)c * S + q) * 2 + 1);
+    }
     nll[c] = a - b;
+    cnt[c] = 0u;  // ready for the next forward
   }
 }
 
 // Backward, per column c (one CTA each): Lambda_k = sum_{k' >= k} d_k' / den_k'
-// (FP64, chunked reverse scan in a fixed order), stored as FP32.
+// in float-float (den_k' split once into a float-float pair, the quotients
+// and a chunked reverse scan in a fixed order; no FP64 division, which costs
+// hundreds of cycles a warp on this GPU), stored as FP32.
 __global__ void __launch_bounds__(256) k_nll_lambda(const double* den, const int32_t* dk, int K, int C, float* lam) {
-  __shared__ double s_chunk[256];
+  __shared__ ff s_suf[256];   // sum of the chunks after chunk q
+  __shared__ ff s_w[8];
   const int c = blockIdx.x;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int ch = (K + 255) / 256;
   const int k0 = min(tid * ch, K), k1 = min(k0 + ch, K);
-  double cs = 0.0;
-  for (int k = k0; k < k1; ++k) cs += (double)dk[k] / den[(size_t)k * C + c];
-  s_chunk[tid] = cs;
+  auto term = [&](int k) { return ff_div(ff{(float)dk[k], 0.f}, d_to_ff(den[(size_t)k * C + c])); };
+  ff cs = ff_zero();
+  for (int k = k0; k < k1; ++k) cs = ff_add(cs, term(k));
+  s_suf[tid] = cs;
   __syncthreads();
-  if (tid == 0) {  // suffix sums of the chunk totals (256 adds)
-    double run = 0.0;
-    for (int q = 255; q >= 0; --q) {
-      const double v = s_chunk[q];
-      s_chunk[q] = run;  // sum of the chunks after q
-      run += v;
-    }
+  // inclusive scan in reverse chunk order: thread t takes chunk 255 - t
+  const ff v = s_suf[255 - tid];
+  const ff incl = warp_inclusive_scan(v, lane);
+  if (lane == 31) s_w[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    const ff t = warp_inclusive_scan(lane < 8 ? s_w[lane] : ff_zero(), lane);
+    const ff ex = shfl_up(t, 1);
+    if (lane < 8) s_w[lane] = lane == 0 ? ff_zero() : ex;
   }
   __syncthreads();
-  double run = s_chunk[tid];
+  const ff up = shfl_up(incl, 1);  // every lane takes part in the shuffle
+  s_suf[255 - tid] = ff_add(s_w[w], lane == 0 ? ff_zero() : up);   // chunks after 255 - t
+  __syncthreads();
+  ff run = s_suf[tid];
   for (int k = k1 - 1; k >= k0; --k) {
-    run += (double)dk[k] / den[(size_t)k * C + c];
-    lam[(size_t)k * C + c] = (float)run;
+    run = ff_add(run, term(k));
+    lam[(size_t)k * C + c] = __fadd_rn(run.hi, run.lo);
   }
 }
 
@@ -593,9 +624,17 @@ int cox_nll_forward(const surv_nll_data* d, const float* B, double* nll, void* s
   if (smem > 48 * 1024)
     NLL_TRY(cuda_err(cudaFuncSetAttribute(k_nll_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                      "smem"));
-  k_nll_finish<<<C, kFinThreads, smem, s>>>(static_cast<float2*>(rec), wt2, wt2 + (size_t)nwarps * C, nwarps, C,
-                                    static_cast<int32_t*>(gend), static_cast<int32_t*>(dk), K, rpw,
-                                    static_cast<double*>(den), nll);
+  // the logs of each column spread over S CTAs (about two waves of the
+  // device's SMs in all), their sums combined by the column's last CTA
+  const int S = std::max(1, std::min(8, (2 * sms) / C));
+  void* fin = nullptr;
+  NLL_TRY(ws_ensure(ws, W::NLL_FIN, sizeof(double) * 2 * (size_t)C * S + sizeof(unsigned) * (size_t)C, &fin));
+  double* fin_part = static_cast<double*>(fin);
+  unsigned* fin_cnt = reinterpret_cast<unsigned*>(fin_part + 2 * (size_t)C * S);
+  NLL_TRY(cuda_err(cudaMemsetAsync(fin_cnt, 0, sizeof(unsigned) * (size_t)C, s), "memset"));
+  k_nll_finish<<<dim3(C, S), kFinThreads, smem, s>>>(static_cast<float2*>(rec), wt2, wt2 + (size_t)nwarps * C, nwarps,
+                                                     C, static_cast<int32_t*>(gend), static_cast<int32_t*>(dk), K, rpw,
+                                                     static_cast<double*>(den), fin_part, fin_cnt, nll);
   NLL_TRY(cuda_err(cudaGetLastError(), "finish"));
   ws->nll_n = n;
   ws->nll_p = (int32_t)p;

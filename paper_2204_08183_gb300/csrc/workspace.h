@@ -19,7 +19,7 @@ struct surv_workspace {
     SLOTS, CTRL, BLOCKCNT, SORTWORK, PERM, PF, WT, AGG,
     // differentiable form (cox_nll_forward / cox_nll_backward)
     NLL_Y, NLL_BCAT, NLL_REC, NLL_WT, NLL_DEN, NLL_LAM, NLL_G, NLL_GB, NLL_GEND, NLL_DK, NLL_WK0, NLL_BLK,
-    NLL_CTRL, NLL_XP, NLL_ERR,
+    NLL_CTRL, NLL_XP, NLL_ERR, NLL_FIN,
     // cross-validated path (cox_cv_path) and lambda_max
     CV_FOLD, CV_DK, CV_DTX, CV_E, CV_ETA, CV_REC, CV_WT, CV_AGG, CV_PART, CV_GCTL, CV_BETA, CV_WIDTH, CV_PEN,
     CV_OUT, CV_FITS, CV_CTRL, CV_DEN, CV_HELD, CV_MEAN, LM_LAM, LM_R, LM_G,
