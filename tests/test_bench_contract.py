@@ -125,3 +125,20 @@ def test_gpu_arms_assemble_the_contract_line(monkeypatch):
         assert e["unit"] == out["unit"] and e["h2d_bytes_per_step"] > 0 and e["d2h_bytes_per_step"] > 0
         assert out["cpu_baseline"]["kind"] == "oracle" and out["cpu_baseline"]["cores"] >= 1
         assert out["config"]["workload"].endswith("n20000_p10")
+
+
+def test_all_cores_oracle_timing(monkeypatch):
+    # one spawned process per core (two here), each a one-sweep fit of its
+    # own column: 3 risk-set passes each, timed from a common barrier
+    sys.path.insert(0, ROOT)
+    try:
+        import bench
+        from paper_2204_08183_gb300 import synth
+    finally:
+        sys.path.remove(ROOT)
+    d = synth.cohort_cox_sparse(20_000, 4, seed=2, density=0.05, n_true=2, laplace_scale=0.2, censor_frac=0.5,
+                                grid=365)
+    monkeypatch.setattr(os, "sched_getaffinity", lambda pid: {0, 1}, raising=False)
+    sps, slowest, passes, cores = bench.oracle_sample_all_cores(d, 2.0)
+    assert cores == 2 and passes == 6
+    assert slowest > 0 and sps == pytest.approx(passes / slowest / (d["p"] + 1))
