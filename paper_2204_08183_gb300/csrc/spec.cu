@@ -574,6 +574,13 @@ __device__ __forceinline__ void ip_sparse(const float* e, const int32_t* gend, c
     ne[b] = end_at(gend, k_lo, k_lo, k_hi, kreg);
     len_max = max(len_max, len[b]);
   }
+  // the row indices of the next rounds are loaded one iteration ahead, so
+  // their DRAM latency overlaps this round's gathers of e
+  int rown[B][SR];
+#pragma unroll
+  for (int b = 0; b < B; ++b)
+#pragma unroll
+    for (int r = 0; r < SR; ++r) rown[b][r] = row0[b][r];
   for (int base = 0; base < len_max; base += 32 * SR) {
     int row[B][SR];
     float ev[B][SR];
@@ -581,8 +588,9 @@ __device__ __forceinline__ void ip_sparse(const float* e, const int32_t* gend, c
     for (int b = 0; b < B; ++b)
 #pragma unroll
       for (int r = 0; r < SR; ++r) {
-        const int i = base + 32 * r + lane;
-        row[b][r] = base == 0 ? row0[b][r] : (i < len[b] ? ld_hint(col[b] + i, strm) : INT_MAX);
+        row[b][r] = rown[b][r];
+        const int i = base + 32 * SR + 32 * r + lane;
+        rown[b][r] = i < len[b] ? ld_hint(col[b] + i, strm) : INT_MAX;
       }
 #pragma unroll
     for (int b = 0; b < B; ++b)
