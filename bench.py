@@ -81,7 +81,7 @@ def parse():
 # kernels as committed: per row pass of the headline batches (k_ipass<4> +
 # k_itrans<4>), per coordinate of the one-coordinate Cox schedule (k_pass +
 # k_btrans) and of the Fine-Gray fit (k_pass + k_btrans).
-TRAFFIC_IND_ROW_PASS = 17290829
+TRAFFIC_IND_ROW_PASS = 17179904
 TRAFFIC_ONE_COORD = 2435456
 TRAFFIC_FG_COORD = 71040486
 # DRAM bytes of one autograd step's four big kernels at N = 2^20, p = 256,
