@@ -107,14 +107,21 @@ def config_dict(n, p, lam):
 
 # --------------------------------------------------------------- clocks
 class ClockSampler:
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi clock and throttle-reason samples every 20 ms, started
+    before the warm-up (its start-up takes longer than a short timed region).
+    begin() and end() bracket the timed region on the host clock; the record
+    keeps the samples whose timestamps fall inside it (20 ms of slack), or
+    every sample when none does."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 20
 
     def __init__(self, index):
         self.index = index
         self.proc = None
         self.path = None
+        self.t0 = self.t1 = None
 
     def start(self):
         try:
@@ -122,10 +129,50 @@ class ClockSampler:
             os.close(fd)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.PERIOD_MS)],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+
+    def begin(self):
+        self.t0 = time.time()
+
+    def end(self):
+        self.t1 = time.time()
+
+    @staticmethod
+    def _stamp(text):
+        # nvidia-smi prints local time as YYYY/MM/DD HH:MM:SS.mmm
+        try:
+            day, clock = text.strip().split(" ")
+            whole, _, frac = clock.partition(".")
+            t = time.mktime(time.strptime(day + " " + whole, "%Y/%m/%d %H:%M:%S"))
+            return t + (float("0." + frac) if frac else 0.0)
+        except Exception:
+            return None
+
+    @classmethod
+    def summarize(cls, rows, t0=None, t1=None):
+        """The clock record of sample rows (lists of the FIELDS values)."""
+        inside = rows
+        window = "whole sampler run"
+        if t0 is not None and t1 is not None:
+            slack = cls.PERIOD_MS / 1e3
+            sel = [r for r in rows if (lambda t: t is not None and t0 - slack <= t <= t1 + slack)(cls._stamp(r[0]))]
+            if sel:
+                inside, window = sel, "timed region"
+        num = lambda v: v.strip().replace(".", "", 1).isdigit()  # noqa: E731
+        sm = [float(r[2]) for r in inside if len(r) > 2 and num(r[2])]
+        mx = [float(r[3]) for r in inside if len(r) > 3 and num(r[3])]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in inside:
+            for k, name in enumerate(names):
+                if len(r) > 6 + k and r[6 + k].strip() == "Active":
+                    reasons.add(name)
+        loaded = [v for v in sm if v > 0.5 * (max(sm) if sm else 1)]
+        return {"sm_mhz": statistics.median(loaded or sm or [0.0]), "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(inside), "window": window}
 
     def stop(self):
         if self.proc is None:
@@ -140,17 +187,7 @@ class ClockSampler:
         os.unlink(self.path)
         if not rows:
             return None
-        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = set()
-        for r in rows:
-            for k, name in enumerate(names):
-                if len(r) > 5 + k and r[5 + k].strip() == "Active":
-                    reasons.add(name)
-        loaded = [s for s in sm if s > 0.5 * (max(sm) if sm else 1)]
-        return {"sm_mhz": statistics.median(loaded or sm or [0.0]), "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(rows)}
+        return self.summarize(rows, self.t0, self.t1)
 
 
 # --------------------------------------------------------------- oracle sample
@@ -283,6 +320,7 @@ def run_gpu(args, rank, world):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     infos = []
     torch.cuda.synchronize()
+    clocks.begin()
     ev0.record(stream)
     for _ in range(args.steps):
         beta_dev.zero_()
@@ -290,6 +328,7 @@ def run_gpu(args, rank, world):
         infos.append(info)
     ev1.record(stream)
     torch.cuda.synchronize()
+    clocks.end()
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
@@ -494,12 +533,14 @@ def run_autograd(args, rank, world):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     evf = torch.cuda.Event(enable_timing=True)
     fwd_ms = 0.0
+    clocks.begin()
     ev0.record(stream)
     for _ in range(args.steps):
         binding.cox_nll_forward(X, t, s, B, ws)
         binding.cox_nll_backward(X, t, s, g, C, ws)
     ev1.record(stream)
     torch.cuda.synchronize()
+    clocks.end()
     ms = ev0.elapsed_time(ev1) / args.steps
     # forward alone, for the split
     ev0.record(stream)
@@ -635,11 +676,13 @@ def run_cv(args, rank, world):
         torch.distributed.barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     res = []
+    clocks.begin()
     ev0.record(stream)
     for _ in range(args.steps):
         res.append(binding.cox_cv_path(sd, fold_d, 10, lam, **kw))
     ev1.record(stream)
     torch.cuda.synchronize()
+    clocks.end()
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
@@ -838,6 +881,7 @@ def run_fg(args, rank, world):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     infos = []
     torch.cuda.synchronize()
+    clocks.begin()
     ev0.record(stream)
     for _ in range(args.steps):
         beta_dev.zero_()
@@ -845,6 +889,7 @@ def run_fg(args, rank, world):
         infos.append(info)
     ev1.record(stream)
     torch.cuda.synchronize()
+    clocks.end()
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()

@@ -142,3 +142,28 @@ def test_all_cores_oracle_timing(monkeypatch):
     sps, slowest, passes, cores = bench.oracle_sample_all_cores(d, 2.0)
     assert cores == 2 and passes == 6
     assert slowest > 0 and sps == pytest.approx(passes / slowest / (d["p"] + 1))
+
+
+def test_clock_record_keeps_the_samples_of_the_timed_region():
+    sys.path.insert(0, ROOT)
+    try:
+        import bench
+    finally:
+        sys.path.remove(ROOT)
+    import time as _time
+    base = _time.mktime(_time.strptime("2026/12/04 12:00:00", "%Y/%m/%d %H:%M:%S"))
+
+    def row(sec, mhz, thermal="Not Active"):
+        stamp = _time.strftime("%Y/%m/%d %H:%M:%S", _time.localtime(base + int(sec))) + ".%03d" % round(
+            (sec % 1) * 1000)
+        return [stamp, "0", str(mhz), "2070", "900.0", "0x0", "Not Active", thermal, "Not Active", "Not Active"]
+
+    rows = [row(0.0, 1200), row(0.5, 1200, "Active"), row(1.00, 2070), row(1.02, 2040), row(1.04, 2070),
+            row(2.0, 1000)]
+    rec = bench.ClockSampler.summarize(rows, base + 0.99, base + 1.05)
+    assert rec["window"] == "timed region" and rec["samples"] == 3
+    assert rec["sm_mhz"] == 2070.0 and rec["sm_max_mhz"] == 2070.0 and rec["reasons"] == []
+    # no sample inside the region: every sample, and the reasons seen anywhere
+    rec = bench.ClockSampler.summarize(rows, base + 3.0, base + 3.01)
+    assert rec["window"] == "whole sampler run" and rec["samples"] == len(rows)
+    assert rec["reasons"] == ["hw_thermal_slowdown"]
