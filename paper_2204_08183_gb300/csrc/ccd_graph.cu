@@ -667,8 +667,10 @@ cudaError_t capture_sweep(const CcdParams& P, bool pdl, cudaStream_t cs, cudaGra
       kp = multi ? k_pass<MODEL, LAYOUT, T, true, true> : k_pass<MODEL, LAYOUT, T, true, false>;
       if constexpr (LAYOUT == 0 && sizeof(T) == 4) {
         // tile shapes the cross-validation tuner may pick
-        if (P.tile_form == 1) kp = multi ? k_pass<MODEL, LAYOUT, T, true, true, 1> : k_pass<MODEL, LAYOUT, T, true, false, 1>;
-        if (P.tile_form == 2) kp = multi ? k_pass<MODEL, LAYOUT, T, true, true, 2> : k_pass<MODEL, LAYOUT, T, true, false, 2>;
+        if (P.tile_form == 1)
+          kp = multi ? k_pass<MODEL, LAYOUT, T, true, true, 1> : k_pass<MODEL, LAYOUT, T, true, false, 1>;
+        if (P.tile_form == 2)
+          kp = multi ? k_pass<MODEL, LAYOUT, T, true, true, 2> : k_pass<MODEL, LAYOUT, T, true, false, 2>;
       }
       kt = k_trans<MODEL, LAYOUT, T, true>;
     } else if (multi) {
