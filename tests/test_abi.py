@@ -250,3 +250,29 @@ def test_noalloc_argument_errors_before_any_device_call(libpath):
     mis = buf[1:1 + 2 * n].reshape(2, n).T                   # 4-byte offset base: not 16-byte aligned
     assert mis.flags["F_CONTIGUOUS"] and mis.ctypes.data % 16 != 0
     assert code(binding.SurvData(t, s, X=mis), "cox", np.zeros(2), 0) == E.SURV_E_INVALID
+
+
+def test_nll_argument_errors_before_any_device_call(libpath):
+    """cox_nll_forward / cox_nll_backward reject a column count outside
+    1..64, host arrays, and a backward with no forward before it on the
+    workspace, before their first CUDA call."""
+    import torch
+    n, p, C = 64, 8, 4
+    X = torch.zeros((n, p), dtype=torch.bfloat16)
+    t = torch.arange(n, 0, -1, dtype=torch.int32)
+    s = torch.ones(n, dtype=torch.int8)
+    ws = binding.Workspace()
+
+    def code(fn, *a):
+        with pytest.raises(binding.SurvError) as ei:
+            fn(*a)
+        return ei.value.code
+
+    E = binding
+    assert code(binding.cox_nll_forward, X, t, s, torch.zeros((p, 65), dtype=torch.float32), ws) == E.SURV_E_INVALID
+    assert code(binding.cox_nll_forward, X, t, s, torch.zeros((p, 0), dtype=torch.float32), ws) == E.SURV_E_INVALID
+    # host tensors: the arrays must be device memory
+    assert code(binding.cox_nll_forward, X, t, s, torch.zeros((p, C), dtype=torch.float32), ws) == E.SURV_E_INVALID
+    # no forward on this workspace yet
+    g = torch.ones(C, dtype=torch.float64)
+    assert code(binding.cox_nll_backward, X, t, s, g, C, ws) == E.SURV_E_INVALID
