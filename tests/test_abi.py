@@ -276,3 +276,25 @@ def test_nll_argument_errors_before_any_device_call(libpath):
     # no forward on this workspace yet
     g = torch.ones(C, dtype=torch.float64)
     assert code(binding.cox_nll_backward, X, t, s, g, C, ws) == E.SURV_E_INVALID
+
+
+def test_sort_and_groups_argument_errors(libpath):
+    """surv_sort_desc and surv_groups reject a negative n and null arrays (and
+    surv_groups a null K) before any CUDA call; n = 0 is a no-op."""
+    import ctypes
+    import numpy as np
+    lib = binding.load()
+    t = np.arange(8, 0, -1, dtype=np.int32)
+    s = np.ones(8, np.int8)
+    perm = np.empty(8, np.int32)
+    tp, sp, pp = (ctypes.c_void_p(a.ctypes.data) for a in (t, s, perm))
+    K = ctypes.c_int64()
+    E = binding
+    assert lib.surv_sort_desc(tp, -1, pp, None) == E.SURV_E_INVALID
+    assert lib.surv_sort_desc(None, 8, pp, None) == E.SURV_E_INVALID
+    assert lib.surv_sort_desc(tp, 8, None, None) == E.SURV_E_INVALID
+    assert lib.surv_sort_desc(tp, 0, pp, None) == E.SURV_OK
+    assert lib.surv_groups(tp, sp, -1, 0, ctypes.byref(K), None, None, None, None) == E.SURV_E_INVALID
+    assert lib.surv_groups(tp, sp, 8, 0, None, None, None, None, None) == E.SURV_E_INVALID
+    assert lib.surv_groups(None, sp, 8, 0, ctypes.byref(K), None, None, None, None) == E.SURV_E_INVALID
+    assert lib.surv_groups(tp, None, 8, 0, ctypes.byref(K), None, None, None, None) == E.SURV_E_INVALID
